@@ -1,0 +1,460 @@
+// FP64 element-wise and reduction kernels of the CCSD iteration: tau / u builders, the packed
+// +/- operands and the unpacking of the particle-particle ladder, residual assembly with the
+// amplitude update (t += R / D, D from the orbital energies), deterministic energy and
+// dot-product reductions (warp shuffles, fixed-order second pass) and the DIIS solve.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ccsd_kernels.h"
+#include "ptx.cuh"
+
+namespace lnocc {
+
+namespace {
+constexpr int kThreads = 256;
+inline int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  return static_cast<int>(b < 152LL * 32 ? (b > 0 ? b : 1) : 152LL * 32);
+}
+#define GRID_STRIDE(idx, total)                                                                          \
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < (total); \
+       idx += static_cast<long long>(gridDim.x) * blockDim.x)
+
+__device__ __forceinline__ int tri_le(int i, int j) { return j * (j + 1) / 2 + i; }  // i <= j
+__device__ __forceinline__ int tri_lt(int i, int j) { return j * (j - 1) / 2 + i; }  // i <  j
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block sum (fixed order within the block); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double sh[32];
+  x = warp_sum(x);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) sh[w] = x;
+  __syncthreads();
+  double y = 0.0;
+  if (w == 0) {
+    y = (l < static_cast<int>(blockDim.x / 32)) ? sh[l] : 0.0;
+    y = warp_sum(y);
+  }
+  __syncthreads();
+  return y;
+}
+
+__device__ __forceinline__ void block_sum_store(double x, double* out) {
+  const double y = block_sum(x);
+  if (threadIdx.x == 0) out[blockIdx.x] = y;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+__global__ void k_tau(const double* t1, const double* t2, double* tau, int o, int v) {
+  const long long total = static_cast<long long>(o) * o * v * v;
+  GRID_STRIDE(idx, total) {
+    const int b = idx % v, a = (idx / v) % v, j = (idx / (v * v)) % o, i = idx / (static_cast<long long>(v) * v * o);
+    tau[idx] = (t2 ? t2[idx] : 0.0) + t1[i * v + a] * t1[j * v + b];
+  }
+}
+
+__global__ void k_u(const double* t2, double* u, int o, int v) {
+  const long long total = static_cast<long long>(o) * o * v * v;
+  const long long vv = static_cast<long long>(v) * v;
+  GRID_STRIDE(idx, total) {
+    const long long ab = idx % vv;
+    const int j = (idx / vv) % o, i = idx / (vv * o);
+    u[idx] = 2.0 * t2[idx] - t2[(static_cast<long long>(j) * o + i) * vv + ab];
+  }
+}
+
+// B+[ij][cd] = w_cd (t_ij^cd + t_ij^dc) / 2 for i<=j, c<=d (w = 1/2 on c = d);
+// B-[ij][cd] = (t_ij^cd - t_ij^dc) / 2 for i<j, c<d.
+template <bool BF16>
+__global__ void k_ladder_ops(const double* t2, void* Bp, void* Bm, int o, int v, int Kpp, int Kpm, long long plane_p,
+                             long long plane_m) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(o) * o * vv;
+  GRID_STRIDE(idx, total) {
+    const int d = idx % v, c = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
+    if (i > j || c > d) continue;
+    const double x = t2[idx];
+    const double y = t2[(static_cast<long long>(i) * o + j) * vv + static_cast<long long>(d) * v + c];
+    const double sp = (c == d ? 0.25 : 0.5) * (x + y);
+    const long long pp = static_cast<long long>(tri_le(i, j)) * Kpp + tri_le(c, d);
+    if (BF16) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(sp, hi, lo);
+      static_cast<__nv_bfloat16*>(Bp)[pp] = hi;
+      static_cast<__nv_bfloat16*>(Bp)[pp + plane_p] = lo;
+    } else {
+      static_cast<double*>(Bp)[pp] = sp;
+    }
+    if (i < j && c < d) {
+      const double sm = 0.5 * (x - y);
+      const long long pm = static_cast<long long>(tri_lt(i, j)) * Kpm + tri_lt(c, d);
+      if (BF16) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(sm, hi, lo);
+        static_cast<__nv_bfloat16*>(Bm)[pm] = hi;
+        static_cast<__nv_bfloat16*>(Bm)[pm + plane_m] = lo;
+      } else {
+        static_cast<double*>(Bm)[pm] = sm;
+      }
+    }
+  }
+}
+
+// R[i][j][a][b] += L+[ab][ij] + sgn(b-a) sgn(j-i) L-[ab][ij]
+__global__ void k_ladder_unpack(const double* Lp, const double* Lm, double* R, int o, int v, int ldp, int ldm) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(o) * o * vv;
+  GRID_STRIDE(idx, total) {
+    const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
+    const int a0 = min(a, b), b0 = max(a, b), i0 = min(i, j), j0 = max(i, j);
+    double L = Lp[static_cast<long long>(tri_le(a0, b0)) * ldp + tri_le(i0, j0)];
+    if (a != b && i != j) {
+      const double s = ((b > a) == (j > i)) ? 1.0 : -1.0;
+      L += s * Lm[static_cast<long long>(tri_lt(a0, b0)) * ldm + tri_lt(i0, j0)];
+    }
+    R[idx] += L;
+  }
+}
+
+// Doubles residual R = Rsym + S + S^(ij)(ab) + P[C2] and update t2n = t2 + R / D.
+// C2_aibj = -1/2 Cp[j,b,i,a] - Cp[i,b,j,a] (Cp[(j,b),(i,a)] = sum_kc t_kj^bc X_kiac).
+__global__ void k_assemble(const double* Rsym, const double* S, const double* Cp, const double* t2, const double* eps,
+                           double* t2n, double* err, double* part, int o, int v) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(o) * o * vv;
+  const long long ov = static_cast<long long>(o) * v;
+  double acc = 0.0;
+  GRID_STRIDE(idx, total) {
+    const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
+    const long long ji_ba = (static_cast<long long>(j) * o + i) * vv + static_cast<long long>(b) * v + a;
+    const double c2 = -0.5 * Cp[(j * v + b) * ov + i * v + a] - Cp[(i * v + b) * ov + j * v + a] -
+                      0.5 * Cp[(i * v + a) * ov + j * v + b] - Cp[(j * v + a) * ov + i * v + b];
+    const double R = Rsym[idx] + S[idx] + S[ji_ba] + c2;
+    const double D = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+    const double d = R / D;
+    t2n[idx] = t2[idx] + d;
+    err[idx] = d;
+    acc += d * d;
+  }
+  block_sum_store(acc, part);
+}
+
+// Singles: R1[i][a] += F_vo[a][i]; t1n = t1 + R1 / (e_i - e_a)
+__global__ void k_update_t1(const double* R1, const double* Fvo, const double* t1, const double* eps, double* t1n,
+                            double* err, double* part, int o, int v) {
+  double acc = 0.0;
+  GRID_STRIDE(idx, static_cast<long long>(o) * v) {
+    const int a = idx % v, i = idx / v;
+    const double R = R1[idx] + Fvo[a * o + i];
+    const double d = R / (eps[i] - eps[o + a]);
+    t1n[idx] = t1[idx] + d;
+    err[idx] = d;
+    acc += d * d;
+  }
+  block_sum_store(acc, part);
+}
+
+// E = sum_ijab (t_ij^ab + t_i^a t_j^b)(2(ia|jb) - (ib|ja)); OVOV[i][a][j][b] = (ia|jb)
+__global__ void k_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(o) * o * vv;
+  double acc = 0.0;
+  GRID_STRIDE(idx, total) {
+    const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
+    const double tau = t2[idx] + (t1 ? t1[i * v + a] * t1[j * v + b] : 0.0);
+    const double iajb = ovov[((static_cast<long long>(i) * v + a) * o + j) * v + b];
+    const double ibja = ovov[((static_cast<long long>(i) * v + b) * o + j) * v + a];
+    acc += tau * (2.0 * iajb - ibja);
+  }
+  block_sum_store(acc, part);
+}
+
+// Fixed-order final sum of `n` partials into out[0].
+__global__ void k_finish_sum(const double* part, int n, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  block_sum_store(acc, out);
+}
+
+// t2mp2[i][j][a][b] = (ia|jb) / (e_i + e_j - e_a - e_b)
+__global__ void k_mp2_amps(const double* ovov, const double* eps, double* t2, int o, int v) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(o) * o * vv;
+  GRID_STRIDE(idx, total) {
+    const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
+    const double iajb = ovov[((static_cast<long long>(i) * v + a) * o + j) * v + b];
+    t2[idx] = iajb / (eps[i] + eps[j] - eps[o + a] - eps[o + b]);
+  }
+}
+
+// dots[k] partials: sum_x e_new[x] * e_all[k][x] for k < m, one block row per k.
+__global__ void k_dots(const double* e_new, const double* e_all, long long len, int m, double* part, int nblk) {
+  const int k = blockIdx.y;
+  double acc = 0.0;
+  for (long long x = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; x < len;
+       x += static_cast<long long>(gridDim.x) * blockDim.x)
+    acc += e_new[x] * e_all[k * len + x];
+  block_sum_store(acc, part + static_cast<long long>(k) * nblk);
+}
+
+__global__ void k_finish_dots(const double* part, int nblk, int m, double* G, int slot, int mmax) {
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[static_cast<long long>(k) * nblk + i];
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) {
+    G[slot * mmax + k] = tot;
+    G[k * mmax + slot] = tot;
+  }
+}
+
+// Pulay DIIS: solve [G 1; 1 0][c; l] = [0; 1] for the m stored vectors (Gaussian elimination with
+// partial pivoting in FP64, one thread). On a singular system the newest vector alone is used.
+__global__ void k_diis_solve(const double* G, int m, int mmax, int newest, double* coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double A[9][10];
+  const int n = m + 1;
+  double scale = 0.0;
+  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(G[i * mmax + i]));
+  if (!(scale > 0.0)) scale = 1.0;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i][j] = G[i * mmax + j] / scale;
+    A[i][m] = -1.0;
+    A[i][n] = 0.0;
+  }
+  for (int j = 0; j < m; ++j) A[m][j] = -1.0;
+  A[m][m] = 0.0;
+  A[m][n] = -1.0;
+  bool ok = true;
+  for (int c = 0; c < n && ok; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+    if (!(fabs(A[p][c]) > 1e-300)) {
+      ok = false;
+      break;
+    }
+    if (p != c)
+      for (int k = 0; k <= n; ++k) {
+        const double t = A[c][k];
+        A[c][k] = A[p][k];
+        A[p][k] = t;
+      }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[r][c] / A[c][c];
+      for (int k = c; k <= n; ++k) A[r][k] -= f * A[c][k];
+    }
+  }
+  double sum = 0.0;
+  if (ok)
+    for (int i = 0; i < m; ++i) {
+      coef[i] = A[i][n] / A[i][i];
+      if (!isfinite(coef[i])) ok = false;
+      sum += coef[i];
+    }
+  if (!ok || !(fabs(sum - 1.0) < 1e-6)) {
+    for (int i = 0; i < m; ++i) coef[i] = (i == newest) ? 1.0 : 0.0;
+  }
+}
+
+// out[x] = sum_k coef[k] * vecs[k][x]
+__global__ void k_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out) {
+  GRID_STRIDE(x, len) {
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc += coef[k] * vecs[k * len + x];
+    out[x] = acc;
+  }
+}
+
+// E_frag = sum_alpha sum_ii' U[i][alpha] E[i][i'] U[i'][alpha]   (one block)
+__global__ void k_project(const double* E, const double* U, int o, int nlo, double* out) {
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < o * o * nlo; idx += blockDim.x) {
+    const int al = idx % nlo, ip = (idx / nlo) % o, i = idx / (nlo * o);
+    acc += U[i * nlo + al] * E[i * o + ip] * U[ip * nlo + al];
+  }
+  block_sum_store(acc, out);
+}
+
+// Lpair[i'][j][a][b] = 2(i'a|jb) - (i'b|ja)
+__global__ void k_pair_L(const double* ovov, double* L, int o, int v) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(o) * o * vv;
+  GRID_STRIDE(idx, total) {
+    const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
+    L[idx] = 2.0 * ovov[((static_cast<long long>(i) * v + a) * o + j) * v + b] -
+             ovov[((static_cast<long long>(i) * v + b) * o + j) * v + a];
+  }
+}
+
+// V+/-[ab][cd] from G[a][c][b][d] = (ac|bd) for rows with a in [a0, a0 + na):
+//   V+ = (ac|bd) + (ad|bc) (a<=b, c<=d),  V- = (ac|bd) - (ad|bc) (a<b, c<d)
+template <bool BF16>
+__global__ void k_pack_vvvv(const double* G, int a0, int na, int v, void* Vp, void* Vm, int Kpp, int Kpm,
+                            long long plane_p, long long plane_m) {
+  const long long vv = static_cast<long long>(v) * v;
+  const long long total = static_cast<long long>(na) * vv * v;  // (a, b, c) then loop d
+  GRID_STRIDE(idx, static_cast<long long>(na) * vv * v) {
+    const int d = idx % v, c = (idx / v) % v, b = (idx / vv) % v, al = idx / (vv * v);
+    const int a = a0 + al;
+    if (a > b || c > d) continue;
+    const double acbd = G[((static_cast<long long>(al) * v + c) * v + b) * v + d];
+    const double adbc = G[((static_cast<long long>(al) * v + d) * v + b) * v + c];
+    const long long pp = static_cast<long long>(tri_le(a, b)) * Kpp + tri_le(c, d);
+    const double xp = acbd + adbc;
+    if (BF16) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(xp, hi, lo);
+      static_cast<__nv_bfloat16*>(Vp)[pp] = hi;
+      static_cast<__nv_bfloat16*>(Vp)[pp + plane_p] = lo;
+    } else {
+      static_cast<double*>(Vp)[pp] = xp;
+    }
+    if (a < b && c < d) {
+      const double xm = acbd - adbc;
+      const long long pm = static_cast<long long>(tri_lt(a, b)) * Kpm + tri_lt(c, d);
+      if (BF16) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(xm, hi, lo);
+        static_cast<__nv_bfloat16*>(Vm)[pm] = hi;
+        static_cast<__nv_bfloat16*>(Vm)[pm + plane_m] = lo;
+      } else {
+        static_cast<double*>(Vm)[pm] = xm;
+      }
+    }
+  }
+  (void)total;
+}
+
+// Dense n x n dressing matrices: X = 1 - T, Y = 1 + T with T[o+a][i] = t_i^a.
+__global__ void k_dress_mats(const double* t1, double* X, double* Y, int o, int v) {
+  const int n = o + v;
+  GRID_STRIDE(idx, static_cast<long long>(n) * n) {
+    const int q = idx % n, p = idx / n;
+    double t = (p >= o && q < o) ? t1[q * v + (p - o)] : 0.0;
+    const double d = (p == q) ? 1.0 : 0.0;
+    X[idx] = d - t;
+    Y[idx] = d + t;
+  }
+}
+
+// xq[Q] = sum_k Boo[Q][k][k]
+__global__ void k_trace_oo(const double* Boo, int naux, int o, double* xq) {
+  GRID_STRIDE(Q, naux) {
+    double s = 0.0;
+    for (int k = 0; k < o; ++k) s += Boo[(static_cast<long long>(Q) * o + k) * o + k];
+    xq[Q] = s;
+  }
+}
+
+// dst[p*ld + q] += alpha * sum_Q B[Q*qstride + p*rstride + q] x[Q]
+__global__ void k_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
+                          int naux, double alpha, double* dst, long long ld) {
+  GRID_STRIDE(idx, static_cast<long long>(rows) * cols) {
+    const int q = idx % cols, p = idx / cols;
+    double acc = 0.0;
+    for (int Q = 0; Q < naux; ++Q) acc += B[Q * qstride + p * rstride + q] * x[Q];
+    dst[p * ld + q] += alpha * acc;
+  }
+}
+
+// NaN / Inf scan; flag[0] = 1 if any
+__global__ void k_finite(const double* x, long long n, int* flag) {
+  GRID_STRIDE(i, n) {
+    if (!isfinite(x[i])) atomicExch(flag, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launch wrappers
+void launch_tau(const double* t1, const double* t2, double* tau, int o, int v, cudaStream_t s) {
+  k_tau<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t1, t2, tau, o, v);
+}
+void launch_u(const double* t2, double* u, int o, int v, cudaStream_t s) {
+  k_u<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t2, u, o, v);
+}
+void launch_ladder_ops(const double* t2, Packed& Bp, Packed& Bm, int o, int v, cudaStream_t s) {
+  const long long pp = 1LL * Bp.rows * Bp.Kp, pm = 1LL * Bm.rows * Bm.Kp;
+  if (Bp.bf16)
+    k_ladder_ops<true><<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t2, Bp.p, Bm.p, o, v, Bp.Kp, Bm.Kp, pp, pm);
+  else
+    k_ladder_ops<false>
+        <<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t2, Bp.p, Bm.p, o, v, Bp.Kp, Bm.Kp, pp, pm);
+}
+void launch_ladder_unpack(const double* Lp, const double* Lm, double* R, int o, int v, int ldp, int ldm,
+                          cudaStream_t s) {
+  k_ladder_unpack<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(Lp, Lm, R, o, v, ldp, ldm);
+}
+int launch_assemble(const double* Rsym, const double* S, const double* Cp, const double* t2, const double* eps,
+                    double* t2n, double* err, double* part, int o, int v, cudaStream_t s) {
+  const int g = grid_for(1LL * o * o * v * v);
+  k_assemble<<<g, kThreads, 0, s>>>(Rsym, S, Cp, t2, eps, t2n, err, part, o, v);
+  return g;
+}
+int launch_update_t1(const double* R1, const double* Fvo, const double* t1, const double* eps, double* t1n,
+                     double* err, double* part, int o, int v, cudaStream_t s) {
+  const int g = grid_for(1LL * o * v);
+  k_update_t1<<<g, kThreads, 0, s>>>(R1, Fvo, t1, eps, t1n, err, part, o, v);
+  return g;
+}
+int launch_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v,
+                  cudaStream_t s) {
+  const int g = grid_for(1LL * o * o * v * v);
+  k_energy<<<g, kThreads, 0, s>>>(t1, t2, ovov, part, o, v);
+  return g;
+}
+void launch_finish_sum(const double* part, int n, double* out, cudaStream_t s) {
+  k_finish_sum<<<1, 1024, 0, s>>>(part, n, out);
+}
+void launch_mp2_amps(const double* ovov, const double* eps, double* t2, int o, int v, cudaStream_t s) {
+  k_mp2_amps<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(ovov, eps, t2, o, v);
+}
+void launch_diis_dots(const double* e_new, const double* e_all, long long len, int m, double* part, double* G,
+                      int slot, int mmax, cudaStream_t s) {
+  const int nblk = 152;
+  k_dots<<<dim3(nblk, m), kThreads, 0, s>>>(e_new, e_all, len, m, part, nblk);
+  k_finish_dots<<<m, kThreads, 0, s>>>(part, nblk, m, G, slot, mmax);
+}
+void launch_diis_solve(const double* G, int m, int mmax, int newest, double* coef, cudaStream_t s) {
+  k_diis_solve<<<1, 32, 0, s>>>(G, m, mmax, newest, coef);
+}
+void launch_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out, cudaStream_t s) {
+  k_extrapolate<<<grid_for(len), kThreads, 0, s>>>(vecs, coef, m, len, out);
+}
+void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s) {
+  k_project<<<1, 256, 0, s>>>(E, U, o, nlo, out);
+}
+void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s) {
+  k_pair_L<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(ovov, L, o, v);
+}
+void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s) {
+  const long long pp = 1LL * Vp.rows * Vp.Kp, pm = 1LL * Vm.rows * Vm.Kp;
+  const long long total = 1LL * na * v * v * v;
+  if (Vp.bf16)
+    k_pack_vvvv<true><<<grid_for(total), kThreads, 0, s>>>(G, a0, na, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+  else
+    k_pack_vvvv<false><<<grid_for(total), kThreads, 0, s>>>(G, a0, na, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+}
+void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s) {
+  k_dress_mats<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(t1, X, Y, o, v);
+}
+void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s) {
+  k_trace_oo<<<grid_for(naux), kThreads, 0, s>>>(Boo, naux, o, xq);
+}
+void launch_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
+                    int naux, double alpha, double* dst, long long ld, cudaStream_t s) {
+  k_coulomb<<<grid_for(1LL * rows * cols), kThreads, 0, s>>>(B, qstride, rows, cols, rstride, x, naux, alpha, dst, ld);
+}
+void launch_finite(const double* x, long long n, int* flag, cudaStream_t s) {
+  k_finite<<<grid_for(n), kThreads, 0, s>>>(x, n, flag);
+}
+
+}  // namespace lnocc

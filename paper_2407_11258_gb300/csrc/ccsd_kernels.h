@@ -1,0 +1,33 @@
+// Launch wrappers of the FP64 element-wise / reduction kernels (ccsd_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace lnocc {
+void launch_tau(const double* t1, const double* t2, double* tau, int o, int v, cudaStream_t s);
+void launch_u(const double* t2, double* u, int o, int v, cudaStream_t s);
+void launch_ladder_ops(const double* t2, Packed& Bp, Packed& Bm, int o, int v, cudaStream_t s);
+void launch_ladder_unpack(const double* Lp, const double* Lm, double* R, int o, int v, int ldp, int ldm,
+                          cudaStream_t s);
+int launch_assemble(const double* Rsym, const double* S, const double* Cp, const double* t2, const double* eps,
+                    double* t2n, double* err, double* part, int o, int v, cudaStream_t s);
+int launch_update_t1(const double* R1, const double* Fvo, const double* t1, const double* eps, double* t1n,
+                     double* err, double* part, int o, int v, cudaStream_t s);
+int launch_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v,
+                  cudaStream_t s);
+void launch_finish_sum(const double* part, int n, double* out, cudaStream_t s);
+void launch_mp2_amps(const double* ovov, const double* eps, double* t2, int o, int v, cudaStream_t s);
+void launch_diis_dots(const double* e_new, const double* e_all, long long len, int m, double* part, double* G,
+                      int slot, int mmax, cudaStream_t s);
+void launch_diis_solve(const double* G, int m, int mmax, int newest, double* coef, cudaStream_t s);
+void launch_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out, cudaStream_t s);
+void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s);
+void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s);
+void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s);
+void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s);
+void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s);
+void launch_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
+                    int naux, double alpha, double* dst, long long ld, cudaStream_t s);
+void launch_finite(const double* x, long long n, int* flag, cudaStream_t s);
+}  // namespace lnocc

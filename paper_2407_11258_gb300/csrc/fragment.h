@@ -1,0 +1,84 @@
+// The fragment handle behind `lnocc_frag`: integrals, amplitudes and workspace on the device.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace lnocc {
+
+// Constant packed operands of the CCSD iteration for one precision.
+struct Consts {
+  Packed kl_cd;  // (kc|ld): rows (k,l), K (c,d)          -> Y_ij^kl
+  Packed kc_ld;  // (kd|lc): rows (k,c), K (l,d)          -> C2 intermediate
+  Packed L;      // 2(ld|kc) - (lc|kd): rows (k,c), K (l,d) -> D2 intermediate
+  Packed c_kld;  // (ld|kc): rows c, K (k,l,d)            -> E2 virtual Fock term
+  Packed kb_cd;  // (kc|bd): rows (k,b), K (c,d)          -> Z_ij^kb
+  Packed Vp, Vm; // packed (ac|bd) +- (ad|bc)             -> particle-particle ladder
+  Packed Bp_t, Bm_t;  // per-iteration packed t+- operands of the ladder
+  bool built = false;
+};
+
+struct Frag {
+  int o = 0, v = 0, N = 0, n = 0;
+  lnocc_opts opts{};
+  bool mixed = true;
+  cudaStream_t s = nullptr;
+
+  // allocation bookkeeping
+  std::vector<void*> allocs;
+  long long device_bytes = 0;
+  bool oom = false;
+  bool scratch_overflow = false;
+  void* alloc(size_t bytes, bool zero = false);
+  Packed alloc_packed(int rows, int K, bool bf16);
+  ~Frag();
+
+  // inputs and constant integrals (FP64)
+  double *eps = nullptr, *Boo = nullptr, *Bov = nullptr, *Bvv = nullptr, *h = nullptr;
+  double *ovov = nullptr, *Lpair = nullptr, *t2mp2 = nullptr;
+  Consts cst[2];  // [0] FP64, [1] BF16 hi/lo
+  Consts& C() { return cst[mixed ? 1 : 0]; }
+  int np_o = 0, nm_o = 0, np_v = 0, nm_v = 0;
+
+  // amplitudes: x = [t1 (o*v) | t2 (o*o*v*v)]
+  double *xcur = nullptr, *xnew = nullptr, *enew = nullptr;
+  // per-iteration work
+  double *Boo_h = nullptr, *Bvo_h = nullptr, *Bvv_h = nullptr;
+  double *Xm = nullptr, *Ym = nullptr, *hh = nullptr, *tmpn = nullptr, *Fh = nullptr, *xq = nullptr;
+  double *tau = nullptr, *u = nullptr, *Rsym = nullptr, *S = nullptr, *Cp = nullptr, *Xk = nullptr, *Yk = nullptr;
+  double *Z = nullptr, *Wb = nullptr, *Wy = nullptr, *R1 = nullptr, *Mtmp = nullptr, *Gooov = nullptr;
+  double *Fvv2 = nullptr, *Foo2 = nullptr, *Eii = nullptr, *Lp_out = nullptr, *Lm_out = nullptr;
+  void *scrA = nullptr, *scrB = nullptr;
+  size_t scr_bytes = 0;
+  // DIIS
+  int dm = 0;
+  double *dvec = nullptr, *derr = nullptr, *G = nullptr, *coef = nullptr, *dpart = nullptr;
+  // reductions / status
+  double *part = nullptr, *scal = nullptr, *h_scal = nullptr;
+  int* dstatus = nullptr;
+
+  // results
+  double e_mp2 = 0.0, e_ccsd = 0.0, last_rms = 0.0;
+  int n_iter = 0;
+  bool converged = false, have_amps = false;
+  double flops_t = 0.0;
+
+  int build(const double* eps_in, const double* B_in);
+  int build_consts(bool bf);
+  int check_device();
+  void contract(const View& a, const View& b, const OutMap& c, bool force_fp64 = false);
+  void contract_packed_b(const View& a, const Packed& PB, int N, const OutMap& c);
+  void iterate(bool fp64_residual);
+  double energy_of(const double* x);
+  int solve(int guess, const double* t1_in, const double* t2_in);
+  int fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double* e_mp2_frag);
+  int triples(int nlo, const double* U, double* e_full, double* e_frag);
+};
+
+}  // namespace lnocc
+
+struct lnocc_frag {
+  lnocc::Frag f;
+};

@@ -1,0 +1,98 @@
+// Internal (host-side) interfaces shared by the translation units of liblnocc.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lnocc.h"
+
+namespace lnocc {
+
+// Device-side error codes written to the status word (host reads it after a sync).
+enum DevErr : int {
+  kDevOk = 0,
+  kDevTimeoutProducer = 1,
+  kDevTimeoutMma = 2,
+  kDevTimeoutEpilogue = 3,
+  kDevBadShape = 4,
+};
+
+// Destination of a contraction: C(m, n) ->
+//   dst[(m / mdiv) * sm1 + (m % mdiv) * sm0 + (n / ndiv) * sn1 + (n % ndiv) * sn0]
+// and dst = alpha * C + beta * dst (beta = 0 overwrites).
+struct OutMap {
+  double* dst;
+  long long sm1, sm0, sn1, sn0;
+  int mdiv, ndiv;
+  double alpha, beta;
+};
+
+inline OutMap out_rowmajor(double* dst, long long ldc, double alpha = 1.0, double beta = 0.0) {
+  return OutMap{dst, 0, ldc, 0, 1, 1 << 30, 1 << 30, alpha, beta};
+}
+
+// A strided FP64 view used as a K-major operand: row r = (r2, r1, r0), column k = (k2, k1, k0)
+// (last index fastest); element (r, k) sits at
+//   src[r2*sr2 + r1*sr1 + r0*sr0 + k2*sk2 + k1*sk1 + k0*sk0] * scale.
+struct View {
+  const double* src;
+  int R2, R1, R0, K2, K1, K0;
+  long long sr2, sr1, sr0, sk2, sk1, sk0;
+  double scale;
+  int rows() const { return R2 * R1 * R0; }
+  int K() const { return K2 * K1 * K0; }
+};
+
+// Helpers to build views: rows(dim, stride) lists from outermost to innermost.
+struct Ax {
+  int n;
+  long long s;
+};
+inline View view(const double* p, Ax r2, Ax r1, Ax r0, Ax k2, Ax k1, Ax k0, double scale = 1.0) {
+  return View{p, r2.n, r1.n, r0.n, k2.n, k1.n, k0.n, r2.s, r1.s, r0.s, k2.s, k1.s, k0.s, scale};
+}
+constexpr Ax kOne{1, 0};
+
+// A packed operand: FP64 [rows][Kp] or BF16 [2][rows][Kp] (hi plane, lo plane).
+struct Packed {
+  void* p = nullptr;
+  int rows = 0, Kp = 0;
+  bool bf16 = false;
+};
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---- kernels (launch wrappers); all enqueue on `s` and do not synchronize
+void pack(const View& v, Packed& out, cudaStream_t s);
+void pack_rows(const View& v, Packed& full, int row0, cudaStream_t s);
+// dst[r*K + k] = view(r, k) + beta * dst[r*K + k]   (FP64, no padding)
+void permute(const View& v, double* dst, double beta, cudaStream_t s);
+void gemm_f64(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s);
+void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,
+             cudaStream_t s, int* dstatus);
+// rows [a_row0, a_row0 + M) of A against rows [b_row0, b_row0 + N) of B
+void gemm_off(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, int K, const OutMap& C,
+              cudaStream_t s, int* dstatus);
+// dispatch on A.bf16
+void gemm(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s,
+          int* dstatus);
+
+struct GemmStats {
+  long long launches = 0;
+  double flops = 0.0;
+};
+GemmStats& gemm_stats();
+
+void set_error(const std::string& msg);
+
+}  // namespace lnocc
+
+#define LN_CUDA(call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      lnocc::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+      return LNOCC_ECUDA;                                                                     \
+    }                                                                                         \
+  } while (0)
