@@ -1,0 +1,326 @@
+"""Benchmark: fragment CCSD(T) on one diamond-like fragment (nocc=16, nvir=240, naux=960), mixed precision.
+
+A step is one pass of the whole per-fragment hot path through the C-ABI: integral assembly
+(lnocc_build_ints), the CCSD solve (lnocc_ccsd), the projected CCSD/MP2 fragment energies
+(lnocc_fragment_energy) and the projected (T) energy (lnocc_triples), on synthetic inputs that stand
+in for the paper's diamond fragment (seeded generator in paper_2407_11258_gb300/synth.py).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-fp64] [--no-cpu]
+
+Prints one JSON line (rank 0). `value` is model TFLOP/s of whole solves with inputs resident in HBM
+(inputs of 0.5 GB exceed the 129 MB L2, so no flush is needed between steps); `e2e` repeats the
+measurement with the inputs in pinned host memory, copied in every step, and the energies read back.
+Multi-GPU runs shard independent fragments (one per rank per step) with no collective in the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fragment CCSD(T) TFLOP/s & solves/s, mixed vs FP64 GPU at |dE|<=1e-6 Eh"
+WORKLOAD = "diamond_like nocc=16 nvir=240 naux=960 projector=2 LMOs"
+
+
+def model_flops(o, v, n_iter):
+    """Work model: CCSD 2o^2v^4 + 16o^3v^3 + 2o^4v^2 per iteration, (T) 6o^3v^4 + 6o^4v^3, assembly 2N(...)."""
+    ccsd = (2 * o**2 * v**4 + 16 * o**3 * v**3 + 2 * o**4 * v**2) * n_iter
+    trip = 6 * o**3 * v**4 + 6 * o**4 * v**3
+    return ccsd, trip
+
+
+def triples_algorithmic_flops(o, v):
+    """Contraction flops the (T) kernels execute per call: every sorted virtual triple once (2o^3v^4 + 2o^4v^3)."""
+    return 2.0 * o**3 * v**4 + 2.0 * o**4 * v**3
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), d.get("hbm_gbs"), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.samples, self.proc, self.idx = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(s[1]) for s in self.samples if len(s) > 2 and s[1].replace(".", "").isdigit()]
+        smax = [float(s[2]) for s in self.samples if len(s) > 2 and s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for k, n in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------------- oracle
+def oracle_triples_sample(fr, t1, t2, jk_pairs):
+    """The oracle's (T) pair-matrix work for the given (j,k) pairs (all i, all abc)."""
+    from oracle import triples as otr
+    ovvv, ovoo, ovov = otr._blocks(fr.B, fr.nocc)
+    eo, ev = fr.eps[:fr.nocc], fr.eps[fr.nocc:]
+    evs = ev[:, None, None] + ev[None, :, None] + ev[None, None, :]
+    tot = 0.0
+    for (j, k) in jk_pairs:
+        zs, ys = [], []
+        for i in range(fr.nocc):
+            W = otr.W_block(i, j, k, t2, ovvv, ovoo)
+            V = otr.V_block(i, j, k, W, t1, ovov)
+            s = np.sqrt(-(eo[i] + eo[j] + eo[k] - evs))
+            w, vv = W / s, V / s
+            zs.append(4 * w + np.einsum("bca->abc", w) + np.einsum("cab->abc", w))
+            ys.append(vv - np.einsum("cba->abc", vv))
+        tot += float(np.sum(np.stack(zs) * np.stack(ys)))
+    return tot
+
+
+def cpu_oracle_rate(fr, budget_s=20.0):
+    """Time the oracle ((T) work for a few (j,k) pairs of this fragment) and convert to model TFLOP/s."""
+    from oracle import ccsd as occ
+    t1 = np.zeros((fr.nocc, fr.nvir))
+    t2 = occ.mp2_amplitudes(fr.eps, fr.B, fr.nocc)
+    pairs, t_used = [], 0.0
+    t0 = time.perf_counter()
+    j = 0
+    while True:
+        pairs.append((j % fr.nocc, (j * 7 + 3) % fr.nocc))
+        oracle_triples_sample(fr, t1, t2, [pairs[-1]])
+        t_used = time.perf_counter() - t0
+        j += 1
+        if t_used > budget_s * 0.5 or j >= fr.nocc * fr.nocc:
+            break
+    _, trip = model_flops(fr.nocc, fr.nvir, 0)
+    share = len(pairs) / float(fr.nocc * fr.nocc)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": trip * share / t_used / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle (T) pair-matrix work for {len(pairs)} of {fr.nocc**2} (j,k) pairs of the "
+                      f"diamond-like fragment ({t_used:.1f} s), scaled by the (T) model flops of those pairs"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores on a bounded sample per step."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2407_11258_gb300 import synth
+    from oracle import ccsd as occ
+    fr = synth.diamond_like()
+    t1 = np.zeros((fr.nocc, fr.nvir))
+    t2 = occ.mp2_amplitudes(fr.eps, fr.B, fr.nocc)
+    _, trip = model_flops(fr.nocc, fr.nvir, 0)
+    flops_step = trip / fr.nocc**2
+    for w in range(args.warmup):
+        oracle_triples_sample(fr, t1, t2, [(w % fr.nocc, (w + 1) % fr.nocc)])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle_triples_sample(fr, t1, t2, [(k % fr.nocc, (3 * k + 1) % fr.nocc)])
+    dt = time.perf_counter() - t0
+    val = flops_step * args.steps / dt / 1e12
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = "oracle (T) pair-matrix work for one (j,k) pair of the diamond-like fragment per step"
+    print(json.dumps({
+        "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+# --------------------------------------------------------------------------------------------- ours
+def solve_once(lnocc, fr_dev, opts, stream):
+    eps, B, U, o, v, q = fr_dev
+    f = lnocc.lnocc_build_ints(o, v, q, eps, B, opts, stream=stream)
+    e, it, _ = lnocc.lnocc_ccsd(f, stream=stream)
+    ec, em = lnocc.lnocc_fragment_energy(f, U, stream=stream)
+    et, etf = lnocc.lnocc_triples(f, U, stream=stream)
+    info = f.info()
+    f.free()
+    return dict(e_ccsd=e, n_iter=it, e_ccsd_frag=ec, e_mp2_frag=em, e_t=et, e_t_frag=etf, e_mp2=info.e_mp2,
+                t_gemm_ms=info.t_triples_gemm_ms, t_triples_ms=info.t_triples_ms, launches=info.kernel_launches)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2407_11258_gb300 import build, lnocc, synth
+    world, rank, local = dist_setup()
+    build.build()
+    lnocc.load()
+    stream = torch.cuda.Stream()
+    # independent fragments per rank (weak scaling): rank r solves the diamond-like fragment with seed 2000+r
+    fr = synth.diamond_like(seed=2000 + rank)
+    o, v, q = fr.nocc, fr.nvir, fr.naux
+    eps_h = torch.tensor(fr.eps).pin_memory()
+    B_h = torch.tensor(fr.B).pin_memory()
+    U_h = torch.tensor(fr.U_frag).pin_memory()
+    with torch.cuda.stream(stream):
+        eps_d, B_d, U_d = eps_h.cuda(non_blocking=True), B_h.cuda(non_blocking=True), U_h.cuda(non_blocking=True)
+    stream.synchronize()
+    opts = lnocc.default_opts(precision=lnocc.LNOCC_PREC_MIXED)
+    fr_dev = (eps_d, B_d, U_d, o, v, q)
+    for _ in range(args.warmup):
+        res = solve_once(lnocc, fr_dev, opts, stream)
+    # ---- device-resident timed region
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    with sampler:
+        ev0.record(stream)
+        runs = [solve_once(lnocc, fr_dev, opts, stream) for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(world, ms)
+    n_iter = runs[-1]["n_iter"]
+    ccsd_f, trip_f = model_flops(o, v, n_iter)
+    flops_solve = ccsd_f + trip_f
+    tflops = world * flops_solve / (ms * 1e-3) / 1e12
+    launches = runs[-1]["launches"] - res["launches"]  # library-wide launch counter across the timed steps
+    # ---- end to end: pinned host inputs copied in, energies read back, every step
+    e2e_ms = None
+    h2d = (eps_h.numel() + B_h.numel() + U_h.numel()) * 8
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            eps_x = eps_h.cuda(non_blocking=True)
+            B_x = B_h.cuda(non_blocking=True)
+            U_x = U_h.cuda(non_blocking=True)
+        solve_once(lnocc, (eps_x, B_x, U_x, o, v, q), opts, stream)
+        del eps_x, B_x, U_x
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(world, (time.perf_counter() - t0) / args.steps * 1e3)
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel: the (T) tensor-core contractions (event-timed per chunk)
+    peak_burst, peak_sust, hbm, peak_src = read_peaks()
+    gemm_ms = float(np.mean([r["t_gemm_ms"] for r in runs]))
+    alg = triples_algorithmic_flops(o, v)
+    achieved = alg / (gemm_ms * 1e-3) / 1e12
+    peak = peak_burst / 3.0  # BF16x3: three bf16 products per useful product
+    out = {
+        "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/fp32 (fp64 update, DIIS, energies)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs (0.5 GB B tensor) larger than L2; no flush",
+                   "ccsd_iterations": n_iter},
+        "solves_per_s": world * 1e3 / ms,
+        "energies": {k: runs[-1][k] for k in ("e_mp2", "e_ccsd", "e_ccsd_frag", "e_mp2_frag", "e_t", "e_t_frag")},
+        "e2e": {"value": world * flops_solve / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 6 * 8},
+        "gpu_launches": launches,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_gemm_tc ((T) W contractions)",
+                     "note": f"useful (T) contraction flops 2o^3v^4+2o^4v^3 per call / event time of those launches; "
+                             f"peak = {peak_src} bf16 burst {peak_burst} / 3 (BF16x3)",
+                     "triples_ms": float(np.mean([r['t_triples_ms'] for r in runs])), "contraction_ms": gemm_ms},
+        "clocks": sampler.summary(),
+    }
+    ref_path = os.path.join(ROOT, "tests", "golden", "oracle_diamond.json")
+    if os.path.exists(ref_path) and rank == 0:
+        ref = json.load(open(ref_path))["diamond_like"]
+        out["abs_err_vs_oracle"] = {k: abs(runs[-1][k] - ref[k]) for k in out["energies"] if k in ref}
+    if not args.no_fp64:
+        opts64 = lnocc.default_opts(precision=lnocc.LNOCC_PREC_FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64 = solve_once(lnocc, fr_dev, opts64, stream)
+        t64 = time.perf_counter() - t0
+        ccsd64, _ = model_flops(o, v, r64["n_iter"])
+        out["fp64_gpu"] = {"ms_per_solve": t64 * 1e3, "value": (ccsd64 + trip_f) / t64 / 1e12, "unit": "TFLOP/s",
+                           "speedup_mixed_vs_fp64": t64 * 1e3 / ms, "n_iter": r64["n_iter"],
+                           "abs_diff_vs_mixed": {k: abs(r64[k] - runs[-1][k]) for k in out["energies"]}}
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_oracle_rate(fr)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -74,6 +74,9 @@ typedef struct lnocc_info {
   double exec_flops;       /* contraction flops issued since build (BF16x3 counted once per product) */
   long long gemm_launches; /* contraction kernel launches since build */
   long long device_bytes;  /* device memory held by the handle */
+  long long kernel_launches; /* library-wide count of kernel launches so far (monotonic) */
+  double t_triples_gemm_ms;  /* last lnocc_triples: device time of its contraction launches (CUDA events) */
+  double t_triples_ms;       /* last lnocc_triples: device time of the whole call (CUDA events) */
 } lnocc_info;
 
 /* Fill `opts` with the defaults listed above (precision = LNOCC_PREC_MIXED). */

@@ -1,6 +1,7 @@
 // extern "C" boundary of liblnocc (declared in include/lnocc.h).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -60,6 +61,8 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
   f.opts = o;
   f.mixed = (o.precision == LNOCC_PREC_MIXED);
   f.s = static_cast<cudaStream_t>(stream);
+  const char* pe = std::getenv("LNOCC_PROFILE");
+  f.prof = pe && pe[0] == '1';
   lnocc::gemm_stats() = lnocc::GemmStats{};
   const int st = f.build(eps, B);
   if (st != LNOCC_OK) {
@@ -79,6 +82,7 @@ int lnocc_ccsd(lnocc_frag* h, const double* t1_in, const double* t2_in, int gues
   }
   Frag& f = h->f;
   f.s = static_cast<cudaStream_t>(stream);
+  f.use_workspace();
   const int st = f.solve(guess_mode, t1_in, t2_in);
   const long long ov = 1LL * f.o * f.v;
   if (f.have_amps) {
@@ -99,6 +103,7 @@ int lnocc_fragment_energy(lnocc_frag* h, int nlo, const double* U_frag, double* 
     return LNOCC_EINVAL;
   }
   h->f.s = static_cast<cudaStream_t>(stream);
+  h->f.use_workspace();
   return h->f.fragment_energy(nlo, U_frag, e_ccsd_frag, e_mp2_frag);
 }
 
@@ -113,6 +118,7 @@ int lnocc_triples(lnocc_frag* h, int nlo, const double* U_frag, double* e_t_full
     return LNOCC_EINVAL;
   }
   h->f.s = static_cast<cudaStream_t>(stream);
+  h->f.use_workspace();
   return h->f.triples(U_frag ? nlo : 0, U_frag, e_t_full, e_t_frag);
 }
 
@@ -134,6 +140,9 @@ int lnocc_frag_info(const lnocc_frag* h, lnocc_info* info) {
   info->exec_flops = lnocc::gemm_stats().flops;
   info->gemm_launches = lnocc::gemm_stats().launches;
   info->device_bytes = f.device_bytes;
+  info->kernel_launches = lnocc::launch_counter();
+  info->t_triples_gemm_ms = f.t_gemm_ms;
+  info->t_triples_ms = f.t_triples_ms;
   return LNOCC_OK;
 }
 
@@ -150,6 +159,9 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
   LN_CUDA(cudaMalloc(&PB.p, static_cast<size_t>(N) * Kp * (bf ? 4 : 8)));
   LN_CUDA(cudaMalloc(&dstatus, 16));
   LN_CUDA(cudaMemsetAsync(dstatus, 0, 16, s));
+  double* ws = nullptr;
+  LN_CUDA(cudaMalloc(&ws, (1u << 22) * sizeof(double)));
+  lnocc::split_ws() = lnocc::SplitWs{ws, 1u << 22};
   const lnocc::Ax one{1, 0};
   lnocc::pack(lnocc::view(A, one, one, lnocc::Ax{M, K}, one, one, lnocc::Ax{K, 1}), PA, s);
   lnocc::pack(lnocc::view(B, one, one, lnocc::Ax{N, K}, one, one, lnocc::Ax{K, 1}), PB, s);
@@ -161,6 +173,8 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
   cudaFree(PA.p);
   cudaFree(PB.p);
   cudaFree(dstatus);
+  cudaFree(ws);
+  lnocc::split_ws() = lnocc::SplitWs{};
   if (e != cudaSuccess) {
     lnocc::set_error(std::string("lnocc_debug_gemm: ") + cudaGetErrorString(e));
     return LNOCC_ECUDA;
@@ -173,6 +187,7 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
 }
 
 int lnocc_free_fragment(lnocc_frag* h) {
+  if (h && lnocc::split_ws().p == h->f.splitk) lnocc::split_ws() = lnocc::SplitWs{};
   delete h;
   return LNOCC_OK;
 }

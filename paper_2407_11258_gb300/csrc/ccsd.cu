@@ -43,7 +43,41 @@ void* Frag::alloc(size_t bytes, bool zero) {
   return p;
 }
 
+void Frag::mark(const char* name) {
+  if (!prof) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  marks.emplace_back(name, e);
+}
+
+void Frag::prof_flush() {
+  if (!prof || marks.empty()) return;
+  cudaEventSynchronize(marks.back().second);
+  for (size_t i = 1; i < marks.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second);
+    prof_ms[marks[i].first] += ms;
+  }
+  for (auto& m : marks) cudaEventDestroy(m.second);
+  marks.clear();
+}
+
+void Frag::prof_print(const char* title) {
+  if (!prof) return;
+  prof_flush();
+  double tot = 0.0;
+  for (auto& kv : prof_ms) tot += kv.second;
+  std::fprintf(stderr, "lnocc profile (%s): total %.3f ms\n", title, tot);
+  std::vector<std::pair<double, std::string>> v;
+  for (auto& kv : prof_ms) v.emplace_back(kv.second, kv.first);
+  std::sort(v.rbegin(), v.rend());
+  for (auto& p : v) std::fprintf(stderr, "  %-14s %10.3f ms  %5.1f%%\n", p.second.c_str(), p.first, 100.0 * p.first / tot);
+  prof_ms.clear();
+}
+
 Frag::~Frag() {
+  for (auto& m : marks) cudaEventDestroy(m.second);
   for (void* p : allocs) cudaFree(p);
   if (h_scal) cudaFreeHost(h_scal);
 }
@@ -175,6 +209,9 @@ int Frag::build(const double* eps_in, const double* B_in) {
   scr_bytes = static_cast<size_t>(cap) * 8;
   scrA = alloc(scr_bytes);
   scrB = alloc(scr_bytes);
+  splitk_cap = 1ull << 22;
+  splitk = static_cast<double*>(alloc(splitk_cap * 8));
+  use_workspace();
   if (oom) {
     set_error("device allocation failed in lnocc_build_ints");
     return LNOCC_ENOMEM;
@@ -344,6 +381,7 @@ void Frag::iterate(bool fp64_residual) {
   const double* t1 = xcur;
   const double* t2 = xcur + ov;
 
+  mark("start");
   // ---- T1-transformed DF factors
   // B^_oo[Q][k][i] = B_oo + sum_c B_ov[Q][k][c] t_i^c
   cudaMemcpyAsync(Boo_h, Boo, N * oo * 8, cudaMemcpyDeviceToDevice, s);
@@ -361,6 +399,7 @@ void Frag::iterate(bool fp64_residual) {
   contract(view(t1, kOne, kOne, A(v, 1), kOne, kOne, A(o, v)), view(Bov, kOne, A(N, ov), A(v, 1), kOne, kOne, A(o, v)),
            OutMap{Bvv_h, 0, v, vv, 1, 1 << 30, v, -1.0, 1.0});
 
+  mark("dress");
   // ---- T1-transformed Fock matrix F^ = (1-T) h (1+T) + sum_Q [2 B^_Qpq x_Q - sum_k B^_Qpk B^_Qkq]
   launch_dress_mats(t1, Xm, Ym, o, v, s);
   contract(view(h, kOne, kOne, A(n, n), kOne, kOne, A(n, 1)), view(Ym, kOne, kOne, A(n, 1), kOne, kOne, A(n, n)),
@@ -392,14 +431,17 @@ void Frag::iterate(bool fp64_residual) {
              view(Bov, kOne, kOne, A(v, 1), kOne, A(N, ov), A(o, v)), out_rowmajor(Fh + o * n + o, n, -1.0, 1.0));
   }
 
+  mark("fock");
   // ---- amplitude-derived arrays
   launch_tau(t1, nullptr, tau, o, v, s);  // t1 (x) t1
   launch_u(t2, u, o, v, s);
 
+  mark("tau_u");
   // ---- Rsym = g^_aibj : (a,i) x (b,j) over Q, written to [i][j][a][b]
   contract(view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
            view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
            OutMap{Rsym, v, o * vv, 1, vv, o, o, 1.0, 0.0});
+  mark("g_aibj");
   // particle-particle ladder with the packed undressed integrals
   launch_ladder_ops(t2, C().Bp_t, C().Bm_t, o, v, s);
   gemm(C().Vp, C().Bp_t, np_v, np_o, np_v, out_rowmajor(Lp_out, np_o), s, dstatus);
@@ -407,6 +449,7 @@ void Frag::iterate(bool fp64_residual) {
     gemm(C().Vm, C().Bm_t, nm_v, nm_o, nm_v, out_rowmajor(Lm_out, nm_o), s, dstatus);
   else cudaMemsetAsync(Lm_out, 0, 8, s);
   launch_ladder_unpack(Lp_out, Lm_out, Rsym, o, v, np_o, std::max(nm_o, 1), s);
+  mark("ladder");
   // Wy[i][j][k][l] = Y_ij^kl = sum_cd (kc|ld) t_ij^cd ; Wb = g^_kilj + Y_ij^kl
   contract_packed_b(view(t2, kOne, kOne, A(static_cast<int>(oo), vv), kOne, kOne, A(static_cast<int>(vv), 1)),
                     C().kl_cd, static_cast<int>(oo), out_rowmajor(Wy, oo));
@@ -414,6 +457,7 @@ void Frag::iterate(bool fp64_residual) {
            view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
            OutMap{Wb, o, oo * o, 1, oo, o, o, 1.0, 0.0});
   permute(view(Wy, kOne, kOne, A(static_cast<int>(oo), oo), kOne, kOne, A(static_cast<int>(oo), 1)), Wb, 1.0, s);
+  mark("Y_Wb");
   // Rsym += sum_kl t_kl^ab Wb_ij^kl + sum_kl t_k^a t_l^b Y_ij^kl   (tau holds t1 (x) t1 here)
   contract(view(Wb, kOne, kOne, A(static_cast<int>(oo), oo), kOne, kOne, A(static_cast<int>(oo), 1)),
            view(t2, kOne, kOne, A(static_cast<int>(vv), 1), kOne, kOne, A(static_cast<int>(oo), vv)),
@@ -422,34 +466,43 @@ void Frag::iterate(bool fp64_residual) {
            view(tau, kOne, kOne, A(static_cast<int>(vv), 1), kOne, kOne, A(static_cast<int>(oo), vv)),
            out_rowmajor(Rsym, vv, 1.0, 1.0));
 
+  mark("hh_ladder");
   // ---- S (pre-P part)
   // Z_ij^kb = sum_cd (kc|bd) t_ij^cd ; S[i][j][a][b] = -sum_k t_k^a Z_ij^kb
   contract_packed_b(view(t2, kOne, kOne, A(static_cast<int>(oo), vv), kOne, kOne, A(static_cast<int>(vv), 1)),
                     C().kb_cd, static_cast<int>(ov), out_rowmajor(Z, ov));
+  mark("Z");
   contract(view(Z, kOne, A(static_cast<int>(oo), ov), A(v, 1), kOne, kOne, A(o, v)),
            view(t1, kOne, kOne, A(v, 1), kOne, kOne, A(o, v)), OutMap{S, vv, 1, 0, v, v, 1 << 30, -1.0, 0.0});
+  mark("ZT");
   // E2: Fvv'_bc = F^_bc - sum_kld u_kl^bd (ld|kc); S += sum_c t_ij^ac Fvv'_bc
   permute(view(Fh + o * n + o, kOne, kOne, A(v, n), kOne, kOne, A(v, 1)), Fvv2, 0.0, s);
   contract_packed_b(view(u, kOne, kOne, A(v, v), kOne, A(static_cast<int>(oo), vv), A(v, 1)), C().c_kld, v,
                     out_rowmajor(Fvv2, v, -1.0, 1.0));
+  mark("Fvv");
   contract(view(t2, kOne, kOne, A(static_cast<int>(oo * v), v), kOne, kOne, A(v, 1)),
            view(Fvv2, kOne, kOne, A(v, v), kOne, kOne, A(v, 1)), out_rowmajor(S, v, 1.0, 1.0));
+  mark("E2a");
   // Foo'_kj = F^_kj + sum_lcd u_lj^cd (kd|lc); S -= sum_k t_ik^ab Foo'_kj
   permute(view(Fh, kOne, kOne, A(o, n), kOne, kOne, A(o, 1)), Foo2, 0.0, s);
   contract(view(ovov, kOne, kOne, A(o, ov * v), A(o, v), A(v, 1), A(v, ov)),
            view(u, kOne, kOne, A(o, vv), A(o, o * vv), A(v, v), A(v, 1)),
            out_rowmajor(Foo2, o, 1.0, 1.0), true);
+  mark("Foo");
   contract(view(t2, kOne, A(o, o * vv), A(static_cast<int>(vv), 1), kOne, kOne, A(o, vv)),
            view(Foo2, kOne, kOne, A(o, 1), kOne, kOne, A(o, o)), OutMap{S, o * vv, 1, 0, vv, static_cast<int>(vv),
                                                                        1 << 30, -1.0, 1.0});
+  mark("E2b");
   // C2 intermediate X_kiac = g^_kiac - 1/2 sum_dl t_li^ad (kd|lc), stored [k][i][a][c]
   contract(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
            view(Bvv_h, kOne, kOne, A(static_cast<int>(vv), 1), kOne, kOne, A(N, vv)), out_rowmajor(Xk, vv));
   contract_packed_b(view(t2, kOne, A(o, vv), A(v, v), kOne, A(o, o * vv), A(v, 1)), C().kc_ld, static_cast<int>(ov),
                     OutMap{Xk, vv, v, o * vv, 1, v, v, -0.5, 1.0});
+  mark("X");
   // Cp[(j,b),(i,a)] = sum_kc t_kj^bc X_kiac
   contract(view(t2, kOne, A(o, vv), A(v, v), kOne, A(o, o * vv), A(v, 1)),
            view(Xk, kOne, A(o, vv), A(v, v), kOne, A(o, o * vv), A(v, 1)), out_rowmajor(Cp, ov));
+  mark("Cp");
   // D2 intermediate Y[i][a][k][c] = 2 g^_aikc - g^_kiac + 1/2 sum_dl u_il^ad L_ldkc
   contract(view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
            view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
@@ -459,17 +512,20 @@ void Frag::iterate(bool fp64_residual) {
            OutMap{Yk, v, ovv, ov, 1, o, v, -1.0, 1.0});
   contract_packed_b(view(u, kOne, A(o, o * vv), A(v, v), kOne, A(o, vv), A(v, 1)), C().L, static_cast<int>(ov),
                     out_rowmajor(Yk, ov, 0.5, 1.0));
+  mark("Yint");
   // S += 1/2 sum_kc u_jk^bc Y_aikc  -> rows (j,b), cols (i,a)
   contract(view(u, kOne, A(o, o * vv), A(v, v), kOne, A(o, vv), A(v, 1)),
            view(Yk, kOne, kOne, A(static_cast<int>(ov), ov), kOne, kOne, A(static_cast<int>(ov), 1)),
            OutMap{S, vv, 1, o * vv, v, v, v, 0.5, 1.0});
 
+  mark("D2");
   // ---- singles residual R1[i][a]
   // A1 via DF: M[Q][d][i] = sum_kc B_Qkc u_ki^cd ; R1 += sum_{Q,d} B^_Qad M[Q][d][i]
   contract(view(Bov, kOne, kOne, A(N, ov), kOne, kOne, A(static_cast<int>(ov), 1)),
            view(u, kOne, A(v, 1), A(o, vv), kOne, A(o, o * vv), A(v, v)), out_rowmajor(Mtmp, ov));
   contract(view(Bvv_h, kOne, kOne, A(v, v), kOne, A(N, vv), A(v, 1)),
            view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)), OutMap{R1, 0, 1, 0, v, 1 << 30, 1 << 30, 1.0, 0.0});
+  mark("A1");
   // B1: R1 -= sum_klc u_kl^ac g^_kilc ; g^_kilc stored [i][k][l][c]
   contract(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
            view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
@@ -477,16 +533,19 @@ void Frag::iterate(bool fp64_residual) {
   contract(view(u, kOne, kOne, A(v, v), kOne, A(static_cast<int>(oo), vv), A(v, 1)),
            view(Gooov, kOne, kOne, A(o, o * ov), kOne, kOne, A(static_cast<int>(o * ov), 1)),
            OutMap{R1, 0, 1, 0, v, 1 << 30, 1 << 30, -1.0, 1.0});
+  mark("B1");
   // C1: R1 += sum_kc u_ik^ac F^_kc
   contract(view(u, kOne, A(o, o * vv), A(v, v), kOne, A(o, vv), A(v, 1)),
            view(Fh + o, kOne, kOne, A(1, 0), kOne, A(o, n), A(v, 1)), out_rowmajor(R1, 1, 1.0, 1.0), true);
 
+  mark("C1");
   // ---- update: t2n = t2 + R/D, t1n = t1 + (R1 + F^_ai)/D1; rms of the update
   const int g2 = launch_assemble(Rsym, S, Cp, t2, eps, xnew + ov, enew + ov, part, o, v, s);
   // F^_vo as [a][i] (row stride n) -> compact copy
   permute(view(Fh + o * n, kOne, kOne, A(v, n), kOne, kOne, A(o, 1)), tmpn, 0.0, s);
   const int g1 = launch_update_t1(R1, tmpn, t1, eps, xnew, enew, part + g2, o, v, s);
   launch_finish_sum(part, g1 + g2, scal + 1, s);
+  mark("update");
   mixed = keep_mixed;
   (void)n2;
 }
@@ -540,9 +599,11 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
       cudaMemcpyAsync(xcur, xnew, L * 8, cudaMemcpyDeviceToDevice, s);
     }
     energy_of(xcur);
+    mark("diis_energy");
     LN_CUDA(cudaMemcpyAsync(h_scal, scal, 16, cudaMemcpyDeviceToHost, s));
     LN_CUDA(cudaStreamSynchronize(s));
     LN_CUDA(cudaGetLastError());
+    prof_flush();
     const double e = h_scal[0];
     const double rms = std::sqrt(h_scal[1] / static_cast<double>(L));
     n_iter = it;
@@ -573,6 +634,7 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
   }
   e_ccsd = e_old;
   have_amps = true;
+  prof_print("ccsd");
   const int st = check_device();
   if (st != LNOCC_OK) return st;
   if (!converged) {

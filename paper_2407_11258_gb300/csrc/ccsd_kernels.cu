@@ -376,13 +376,16 @@ __global__ void k_finite(const double* x, long long n, int* flag) {
 // ---------------------------------------------------------------------------------------------
 // launch wrappers
 void launch_tau(const double* t1, const double* t2, double* tau, int o, int v, cudaStream_t s) {
+  count_launch();
   k_tau<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t1, t2, tau, o, v);
 }
 void launch_u(const double* t2, double* u, int o, int v, cudaStream_t s) {
+  count_launch();
   k_u<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t2, u, o, v);
 }
 void launch_ladder_ops(const double* t2, Packed& Bp, Packed& Bm, int o, int v, cudaStream_t s) {
   const long long pp = 1LL * Bp.rows * Bp.Kp, pm = 1LL * Bm.rows * Bm.Kp;
+  count_launch();
   if (Bp.bf16)
     k_ladder_ops<true><<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(t2, Bp.p, Bm.p, o, v, Bp.Kp, Bm.Kp, pp, pm);
   else
@@ -391,69 +394,86 @@ void launch_ladder_ops(const double* t2, Packed& Bp, Packed& Bm, int o, int v, c
 }
 void launch_ladder_unpack(const double* Lp, const double* Lm, double* R, int o, int v, int ldp, int ldm,
                           cudaStream_t s) {
+  count_launch();
   k_ladder_unpack<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(Lp, Lm, R, o, v, ldp, ldm);
 }
 int launch_assemble(const double* Rsym, const double* S, const double* Cp, const double* t2, const double* eps,
                     double* t2n, double* err, double* part, int o, int v, cudaStream_t s) {
   const int g = grid_for(1LL * o * o * v * v);
+  count_launch();
   k_assemble<<<g, kThreads, 0, s>>>(Rsym, S, Cp, t2, eps, t2n, err, part, o, v);
   return g;
 }
 int launch_update_t1(const double* R1, const double* Fvo, const double* t1, const double* eps, double* t1n,
                      double* err, double* part, int o, int v, cudaStream_t s) {
   const int g = grid_for(1LL * o * v);
+  count_launch();
   k_update_t1<<<g, kThreads, 0, s>>>(R1, Fvo, t1, eps, t1n, err, part, o, v);
   return g;
 }
 int launch_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v,
                   cudaStream_t s) {
   const int g = grid_for(1LL * o * o * v * v);
+  count_launch();
   k_energy<<<g, kThreads, 0, s>>>(t1, t2, ovov, part, o, v);
   return g;
 }
 void launch_finish_sum(const double* part, int n, double* out, cudaStream_t s) {
+  count_launch();
   k_finish_sum<<<1, 1024, 0, s>>>(part, n, out);
 }
 void launch_mp2_amps(const double* ovov, const double* eps, double* t2, int o, int v, cudaStream_t s) {
+  count_launch();
   k_mp2_amps<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(ovov, eps, t2, o, v);
 }
 void launch_diis_dots(const double* e_new, const double* e_all, long long len, int m, double* part, double* G,
                       int slot, int mmax, cudaStream_t s) {
   const int nblk = 152;
+  count_launch();
   k_dots<<<dim3(nblk, m), kThreads, 0, s>>>(e_new, e_all, len, m, part, nblk);
+  count_launch();
   k_finish_dots<<<m, kThreads, 0, s>>>(part, nblk, m, G, slot, mmax);
 }
 void launch_diis_solve(const double* G, int m, int mmax, int newest, double* coef, cudaStream_t s) {
+  count_launch();
   k_diis_solve<<<1, 32, 0, s>>>(G, m, mmax, newest, coef);
 }
 void launch_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out, cudaStream_t s) {
+  count_launch();
   k_extrapolate<<<grid_for(len), kThreads, 0, s>>>(vecs, coef, m, len, out);
 }
 void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s) {
+  count_launch();
   k_project<<<1, 256, 0, s>>>(E, U, o, nlo, out);
 }
 void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s) {
+  count_launch();
   k_pair_L<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(ovov, L, o, v);
 }
 void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s) {
   const long long pp = 1LL * Vp.rows * Vp.Kp, pm = 1LL * Vm.rows * Vm.Kp;
   const long long total = 1LL * na * v * v * v;
+  count_launch();
   if (Vp.bf16)
     k_pack_vvvv<true><<<grid_for(total), kThreads, 0, s>>>(G, a0, na, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
   else
     k_pack_vvvv<false><<<grid_for(total), kThreads, 0, s>>>(G, a0, na, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
 }
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s) {
+  count_launch();
   k_dress_mats<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(t1, X, Y, o, v);
 }
 void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s) {
+  count_launch();
   k_trace_oo<<<grid_for(naux), kThreads, 0, s>>>(Boo, naux, o, xq);
 }
 void launch_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
                     int naux, double alpha, double* dst, long long ld, cudaStream_t s) {
+  count_launch();
   k_coulomb<<<grid_for(1LL * rows * cols), kThreads, 0, s>>>(B, qstride, rows, cols, rstride, x, naux, alpha, dst, ld);
 }
 void launch_finite(const double* x, long long n, int* flag, cudaStream_t s) {
+  count_launch();
   k_finite<<<grid_for(n), kThreads, 0, s>>>(x, n, flag);
 }
 

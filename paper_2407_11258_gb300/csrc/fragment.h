@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -52,6 +54,9 @@ struct Frag {
   double *Fvv2 = nullptr, *Foo2 = nullptr, *Eii = nullptr, *Lp_out = nullptr, *Lm_out = nullptr;
   void *scrA = nullptr, *scrB = nullptr;
   size_t scr_bytes = 0;
+  double* splitk = nullptr;  // split-K partials workspace
+  size_t splitk_cap = 0;
+  void use_workspace() { split_ws() = SplitWs{splitk, splitk_cap}; }
   // DIIS
   int dm = 0;
   double *dvec = nullptr, *derr = nullptr, *G = nullptr, *coef = nullptr, *dpart = nullptr;
@@ -64,6 +69,15 @@ struct Frag {
   int n_iter = 0;
   bool converged = false, have_amps = false;
   double flops_t = 0.0;
+  double t_gemm_ms = 0.0, t_triples_ms = 0.0;  // device times of the last lnocc_triples
+
+  // optional per-step timing (environment LNOCC_PROFILE=1): events between named marks
+  bool prof = false;
+  std::vector<std::pair<std::string, cudaEvent_t>> marks;
+  std::map<std::string, double> prof_ms;
+  void mark(const char* name);
+  void prof_flush();
+  void prof_print(const char* title);
 
   int build(const double* eps_in, const double* B_in);
   int build_consts(bool bf);

@@ -21,6 +21,11 @@ GemmStats& gemm_stats() {
   return s;
 }
 
+long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Packing
 // ------------------------------------------------------------------------------------------------
@@ -61,6 +66,7 @@ void pack(const View& v, Packed& out, cudaStream_t s) {
   const long long total = static_cast<long long>(out.rows) * out.Kp;
   const int threads = 256;
   const int blocks = static_cast<int>(std::min<long long>((total + threads - 1) / threads, 152LL * 32));
+  count_launch();
   if (out.bf16)
     k_pack<true><<<blocks, threads, 0, s>>>(v, out.p, out.Kp, total);
   else
@@ -74,6 +80,7 @@ void pack_rows(const View& v, Packed& full, int row0, cudaStream_t s) {
   const int blocks = static_cast<int>(std::min<long long>((total + threads - 1) / threads, 152LL * 32));
   const long long plane = static_cast<long long>(full.rows) * full.Kp;
   const size_t off = static_cast<size_t>(row0) * full.Kp;
+  count_launch();
   if (full.bf16)
     k_pack<true><<<blocks, threads, 0, s>>>(v, static_cast<__nv_bfloat16*>(full.p) + off, full.Kp, plane);
   else
@@ -97,28 +104,49 @@ void permute(const View& v, double* dst, double beta, cudaStream_t s) {
   if (total <= 0) return;
   const int threads = 256;
   const int blocks = static_cast<int>(std::min<long long>((total + threads - 1) / threads, 152LL * 32));
+  count_launch();
   k_permute<<<blocks, threads, 0, s>>>(v, dst, beta);
 }
 
-__device__ __forceinline__ void store_out(const OutMap& C, int m, int n, double acc) {
-  const long long off = static_cast<long long>(m / C.mdiv) * C.sm1 + static_cast<long long>(m % C.mdiv) * C.sm0 +
-                        static_cast<long long>(n / C.ndiv) * C.sn1 + static_cast<long long>(n % C.ndiv) * C.sn0;
-  double r = C.alpha * acc;
-  if (C.beta != 0.0) r += C.beta * C.dst[off];
-  C.dst[off] = r;
+__device__ __forceinline__ void store_out(const OutMap& C, int m, int n, double acc, long long base = 0) {
+  const long long off = base + static_cast<long long>(m / C.mdiv) * C.sm1 +
+                        static_cast<long long>(m % C.mdiv) * C.sm0 + static_cast<long long>(n / C.ndiv) * C.sn1 +
+                        static_cast<long long>(n % C.ndiv) * C.sn0;
+  if (C.dst32) {
+    float r = static_cast<float>(C.alpha * acc);
+    if (C.beta != 0.0) r += static_cast<float>(C.beta) * C.dst32[off];
+    C.dst32[off] = r;
+  } else {
+    double r = C.alpha * acc;
+    if (C.beta != 0.0) r += C.beta * C.dst[off];
+    C.dst[off] = r;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
 // FP64 SIMT GEMM: 64x64 tile, 16-wide K steps, 256 threads with 4x4 outputs each.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, const double* __restrict__ B,
-                                                  int M, int N, int Kp, OutMap C) {
+                                                  int M, int N, int Kp, OutMap C, int ksplit, double* ws,
+                                                  const BatchEntry* __restrict__ batch) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  long long cbase = 0;
+  int kbeg = blockIdx.z * ksplit, kend = min(Kp, kbeg + ksplit);
+  if (batch) {  // one problem per blockIdx.z; no split-K
+    const BatchEntry be = batch[blockIdx.z];
+    if (m0 >= be.M) return;
+    A += static_cast<long long>(be.a_row0) * Kp;
+    B += static_cast<long long>(be.b_row0) * Kp;
+    M = be.M;
+    cbase = be.cbase;
+    kbeg = 0;
+    kend = Kp;
+  }
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < Kp; k0 += 16) {
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int e = threadIdx.x; e < 64 * 16; e += 256) {
       const int r = e / 16, k = e % 16;
       const int m = m0 + r, n = n0 + r;
@@ -145,15 +173,64 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-      if (m < M && n < N) store_out(C, m, n, acc[i][j]);
+      if (m < M && n < N) {
+        if (ws)
+          ws[(static_cast<long long>(blockIdx.z) * M + m) * N + n] = acc[i][j];
+        else
+          store_out(C, m, n, acc[i][j], cbase);
+      }
     }
+}
+
+// Fixed-order sum of split-K partials ws[split][M][N], then the OutMap store.
+__global__ void k_splitk_reduce(const double* __restrict__ ws, int splits, int M, int N, OutMap C) {
+  const long long total = static_cast<long long>(M) * N;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += ws[z * total + idx];
+    store_out(C, static_cast<int>(idx / N), static_cast<int>(idx % N), acc);
+  }
+}
+
+SplitWs& split_ws() {
+  static SplitWs w;
+  return w;
+}
+
+// Number of K splits: enough CTAs to cover the SMs twice, at least 4 K blocks per split, and the
+// partials must fit the workspace.
+static int choose_splits(long long tiles, int nkb, long long MN) {
+  if (tiles >= 76 || nkb < 8) return 1;
+  long long s = (304 + tiles - 1) / tiles;
+  s = std::min<long long>(s, nkb / 4);
+  const SplitWs& w = split_ws();
+  if (!w.p) return 1;
+  s = std::min<long long>(s, static_cast<long long>(w.cap / std::max<long long>(MN, 1)));
+  if (s < 2) return 1;
+  const int per = (nkb + static_cast<int>(s) - 1) / static_cast<int>(s);
+  return (nkb + per - 1) / per;  // no empty split
+}
+
+static void splitk_reduce(int splits, int M, int N, const OutMap& C, cudaStream_t s) {
+  const long long total = static_cast<long long>(M) * N;
+  const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 8));
+  count_launch();
+  k_splitk_reduce<<<blocks, 256, 0, s>>>(split_ws().p, splits, M, N, C);
 }
 
 void gemm_f64(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s) {
   (void)K;
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), M, N, A.Kp,
-                                  C);
+  const long long tiles = static_cast<long long>((N + 63) / 64) * ((M + 63) / 64);
+  const int nk16 = A.Kp / 16;
+  const int splits = choose_splits(tiles, nk16 / 4, static_cast<long long>(M) * N);
+  const int per = splits > 1 ? ((nk16 + splits - 1) / splits) * 16 : A.Kp;
+  const int nsplit = splits > 1 ? (A.Kp + per - 1) / per : 1;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, nsplit);
+  count_launch();
+  k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), M, N, A.Kp, C,
+                                  per, nsplit > 1 ? split_ws().p : nullptr, nullptr);
+  if (nsplit > 1) splitk_reduce(nsplit, M, N, C, s);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -177,8 +254,22 @@ struct TcCfg {
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M, int N,
-              int nkb, OutMap C, int* status, int a_row0, int b_row0) {
+              int nkb_total, OutMap C, int* status, int a_row0, int b_row0, int kb_per, double* ws,
+              const BatchEntry* __restrict__ batch) {
   using Cfg = TcCfg<BN>;
+  int kb0 = blockIdx.z * kb_per;
+  int nkb = min(nkb_total - kb0, kb_per);
+  long long cbase = 0;
+  if (batch) {  // one problem per blockIdx.z (rows [a_row0, a_row0 + M) of A); no split-K
+    const BatchEntry be = batch[blockIdx.z];
+    if (static_cast<int>(blockIdx.y) * Cfg::BM >= be.M) return;
+    a_row0 = be.a_row0;
+    b_row0 = be.b_row0;
+    M = be.M;
+    cbase = be.cbase;
+    kb0 = 0;
+    nkb = nkb_total;
+  }
   constexpr int S = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -219,10 +310,11 @@ __global__ void __launch_bounds__(128, 1)
       }
       uint8_t* st = smem + s * Cfg::STAGE_BYTES;
       mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-      tma_load_3d(st, &tA, &full[s], kb * Cfg::BK, a_row0 + m0, 0);
-      tma_load_3d(st + Cfg::A_BYTES, &tA, &full[s], kb * Cfg::BK, a_row0 + m0, 1);
-      tma_load_3d(st + 2 * Cfg::A_BYTES, &tB, &full[s], kb * Cfg::BK, b_row0 + n0, 0);
-      tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tB, &full[s], kb * Cfg::BK, b_row0 + n0, 1);
+      const int kc = (kb0 + kb) * Cfg::BK;
+      tma_load_3d(st, &tA, &full[s], kc, a_row0 + m0, 0);
+      tma_load_3d(st + Cfg::A_BYTES, &tA, &full[s], kc, a_row0 + m0, 1);
+      tma_load_3d(st + 2 * Cfg::A_BYTES, &tB, &full[s], kc, b_row0 + n0, 0);
+      tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tB, &full[s], kc, b_row0 + n0, 1);
       ++issued;
     }
     if (!ok) {  // let the copies already in flight land before the CTA retires
@@ -272,7 +364,12 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c0 + j;
-          if (n < N) store_out(C, m, n, static_cast<double>(v[j]));
+          if (n < N) {
+            if (ws)
+              ws[(static_cast<long long>(blockIdx.z) * M + m) * N + n] = static_cast<double>(v[j]);
+            else
+              store_out(C, m, n, static_cast<double>(v[j]), cbase);
+          }
         }
       }
     }
@@ -329,8 +426,62 @@ static void launch_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, 
     set_error("cuTensorMapEncodeTiled failed");
     return;
   }
-  dim3 grid((N + BN - 1) / BN, (M + Cfg::BM - 1) / Cfg::BM);
-  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM, s>>>(ta, tb, M, N, A.Kp / 64, C, dstatus, a_row0, b_row0);
+  const long long tiles = static_cast<long long>((N + BN - 1) / BN) * ((M + Cfg::BM - 1) / Cfg::BM);
+  const int nkb = A.Kp / 64;
+  const int splits = choose_splits(tiles, nkb, static_cast<long long>(M) * N);
+  const int per = (nkb + splits - 1) / splits;
+  dim3 grid((N + BN - 1) / BN, (M + Cfg::BM - 1) / Cfg::BM, splits);
+  count_launch();
+  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM, s>>>(ta, tb, M, N, nkb, C, dstatus, a_row0, b_row0, per,
+                                              splits > 1 ? split_ws().p : nullptr, nullptr);
+  if (splits > 1) splitk_reduce(splits, M, N, C, s);
+}
+
+template <int BN>
+static void launch_tc_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N,
+                              const OutMap& C, cudaStream_t s, int* dstatus) {
+  using Cfg = TcCfg<BN>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    attr = true;
+  }
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, Cfg::BM) || !make_map(&tb, B, BN)) {
+    set_error("cuTensorMapEncodeTiled failed");
+    return;
+  }
+  dim3 grid((N + BN - 1) / BN, (maxM + Cfg::BM - 1) / Cfg::BM, nbatch);
+  count_launch();
+  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM, s>>>(ta, tb, maxM, N, A.Kp / 64, C, dstatus, 0, 0, A.Kp / 64, nullptr,
+                                              dbatch);
+}
+
+void gemm_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N, int K,
+                  const OutMap& C, cudaStream_t s, int* dstatus) {
+  if (nbatch <= 0 || maxM <= 0 || N <= 0) return;
+  GemmStats& st = gemm_stats();
+  st.launches++;
+  st.flops += 2.0 * maxM * N * K * nbatch * 0.5;  // rows shrink along the batch; counted as half
+  if (A.bf16) {
+    if (N <= 32)
+      launch_tc_batched<32>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
+    else if (N <= 64)
+      launch_tc_batched<64>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
+    else if (N <= 128)
+      launch_tc_batched<128>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
+    else if (N <= 144)
+      launch_tc_batched<144>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
+    else if (N <= 192)
+      launch_tc_batched<192>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
+    else
+      launch_tc_batched<256>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
+  } else {
+    dim3 grid((N + 63) / 64, (maxM + 63) / 64, nbatch);
+    count_launch();
+    k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), maxM, N, A.Kp,
+                                    C, A.Kp, nullptr, dbatch);
+  }
 }
 
 void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,

@@ -21,16 +21,25 @@ enum DevErr : int {
 // Destination of a contraction: C(m, n) ->
 //   dst[(m / mdiv) * sm1 + (m % mdiv) * sm0 + (n / ndiv) * sn1 + (n % ndiv) * sn0]
 // and dst = alpha * C + beta * dst (beta = 0 overwrites).
+// When dst32 is set the destination is FP32 instead (dst unused).
 struct OutMap {
   double* dst;
   long long sm1, sm0, sn1, sn0;
   int mdiv, ndiv;
   double alpha, beta;
+  float* dst32 = nullptr;
 };
 
 inline OutMap out_rowmajor(double* dst, long long ldc, double alpha = 1.0, double beta = 0.0) {
   return OutMap{dst, 0, ldc, 0, 1, 1 << 30, 1 << 30, alpha, beta};
 }
+
+// One problem of a batched GEMM: rows [a_row0, a_row0 + M) of A against rows [b_row0, b_row0 + N) of B,
+// destination offset cbase (elements) added to the OutMap.
+struct BatchEntry {
+  int a_row0, b_row0, M, pad;
+  long long cbase;
+};
 
 // A strided FP64 view used as a K-major operand: row r = (r2, r1, r0), column k = (k2, k1, k0)
 // (last index fastest); element (r, k) sits at
@@ -74,15 +83,27 @@ void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, in
 // rows [a_row0, a_row0 + M) of A against rows [b_row0, b_row0 + N) of B
 void gemm_off(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, int K, const OutMap& C,
               cudaStream_t s, int* dstatus);
+void gemm_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N, int K,
+                  const OutMap& C, cudaStream_t s, int* dstatus);
 // dispatch on A.bf16
 void gemm(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s,
           int* dstatus);
+
+// Workspace for split-K partials (FP64 elements), provided by the caller of the contraction engine.
+struct SplitWs {
+  double* p = nullptr;
+  size_t cap = 0;
+};
+SplitWs& split_ws();
 
 struct GemmStats {
   long long launches = 0;
   double flops = 0.0;
 };
 GemmStats& gemm_stats();
+// Library-wide count of kernel launches issued by the host wrappers (monotonic).
+long long& launch_counter();
+inline void count_launch(long long n = 1) { launch_counter() += n; }
 
 void set_error(const std::string& msg);
 

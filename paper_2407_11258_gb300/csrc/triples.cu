@@ -134,6 +134,120 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
   }
 }
 
+// Staged block energy: one CTA per (pair, a), a <= b. w = W s and v = (W + disconnected) s are formed once
+// per block in shared memory (Real = float on the mixed path, double on the FP64 path), with
+// s = 1/sqrt(-Delta) and -Delta = d_i + d_j + d_k, d_m = (e_a + e_b + e_c)/3 - e_m > 0 evaluated in FP64
+// (a sum of positive terms: no cancellation when it is rounded to Real). Threads then run over (j, k)
+// and every distinct ordering of (a, b, c); the i-sums are accumulated in Real and the block sum in FP64.
+template <typename TW, typename Real>
+__global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, const int* __restrict__ pb,
+                                  const int* __restrict__ pc, int pair0, int o, int v, const double* __restrict__ eps,
+                                  const double* __restrict__ t1, const double* __restrict__ ovov,
+                                  const double* __restrict__ U, int nlo, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int slot = blockIdx.y, a = blockIdx.x;
+  const int b = pb[pair0 + slot], c = pc[pair0 + slot];
+  const long long blk_id = (1LL * (pair0 + slot)) * v + a;
+  if (a > b) {
+    if (threadIdx.x == 0) out[2 * blk_id] = out[2 * blk_id + 1] = 0.0;
+    return;
+  }
+  const int o2 = o * o, o3 = o2 * o;
+  Real* sw = reinterpret_cast<Real*>(smraw);
+  Real* sv = sw + o3;
+  Real* Sab = sv + o3;      // (y0 a|y1 b)
+  Real* Sac = Sab + o2;     // (y0 a|y2 c)
+  Real* Sbc = Sac + o2;     // (y1 b|y2 c)
+  Real* ta = Sbc + o2;      // t1[y][a], t1[y][b], t1[y][c]
+  Real* tb = ta + o;
+  Real* tc = tb + o;
+  Real* dm = tc + o;        // d_m
+  Real* Us = dm + o;        // U[i][alpha]
+  const long long ov = 1LL * o * v;
+  const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
+  for (int idx = threadIdx.x; idx < o2; idx += blockDim.x) {
+    const int p = idx / o, q = idx % o;
+    Sab[idx] = static_cast<Real>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + b]);
+    Sac[idx] = static_cast<Real>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + c]);
+    Sbc[idx] = static_cast<Real>(ovov[(1LL * p * v + b) * ov + 1LL * q * v + c]);
+  }
+  for (int y = threadIdx.x; y < o; y += blockDim.x) {
+    ta[y] = static_cast<Real>(t1[y * v + a]);
+    tb[y] = static_cast<Real>(t1[y * v + b]);
+    tc[y] = static_cast<Real>(t1[y * v + c]);
+    dm[y] = static_cast<Real>(ex3 - eps[y]);
+  }
+  for (int idx = threadIdx.x; idx < o * nlo; idx += blockDim.x) Us[idx] = static_cast<Real>(U[idx]);
+  __syncthreads();
+  const TW* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
+  for (int idx = threadIdx.x; idx < o3; idx += blockDim.x) {
+    const int y0 = idx / o2, y1 = (idx / o) % o, y2 = idx % o;
+    const Real Wv = static_cast<Real>(Wb[idx]);
+    const Real disc = Sab[y0 * o + y1] * tc[y2] + Sac[y0 * o + y2] * tb[y1] + Sbc[y1 * o + y2] * ta[y0];
+    const Real d = dm[y0] + dm[y1] + dm[y2];
+    Real sc;
+    if (sizeof(Real) == 4)
+      sc = static_cast<Real>(rsqrtf(static_cast<float>(d)));
+    else
+      sc = static_cast<Real>(1.0 / sqrt(static_cast<double>(d)));
+    sw[idx] = Wv * sc;
+    sv[idx] = (Wv + disc) * sc;
+  }
+  __syncthreads();
+  const int x[3] = {a, b, c};
+  const int S3[3] = {o2, o, 1};
+  double e_can = 0.0, e_frag = 0.0;
+  for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
+    const int j = jk / o, k = jk % o;
+    for (int pi = 0; pi < 6; ++pi) {
+      const int p0 = kPerm[pi][0], p1 = kPerm[pi][1], p2 = kPerm[pi][2];
+      bool dup = false;
+      for (int q = 0; q < pi && !dup; ++q)
+        dup = x[kPerm[q][0]] == x[p0] && x[kPerm[q][1]] == x[p1] && x[kPerm[q][2]] == x[p2];
+      if (dup) continue;
+      // offsets of W^{abc}_y for the four orderings: T (p0,p1,p2), T o c (p1,p2,p0), T o c^2 (p2,p0,p1),
+      // reversed (p2,p1,p0); slot p receives i, j or k.
+      const int base0 = j * S3[p1] + k * S3[p2], si0 = S3[p0];
+      const int base1 = j * S3[p2] + k * S3[p0], si1 = S3[p1];
+      const int base2 = j * S3[p0] + k * S3[p1], si2 = S3[p2];
+      const int base3 = j * S3[p1] + k * S3[p0], si3 = S3[p2];
+      Real acc = 0, zu[8], yu[8];
+      for (int al = 0; al < 8; ++al) zu[al] = yu[al] = 0;
+      for (int i = 0; i < o; ++i) {
+        const Real z = 4 * sw[base0 + i * si0] + sw[base1 + i * si1] + sw[base2 + i * si2];
+        const Real y = sv[base0 + i * si0] - sv[base3 + i * si3];
+        acc += z * y;
+        for (int al = 0; al < nlo; ++al) {
+          zu[al] += Us[i * nlo + al] * z;
+          yu[al] += Us[i * nlo + al] * y;
+        }
+      }
+      e_can += static_cast<double>(acc);
+      for (int al = 0; al < nlo; ++al) e_frag += static_cast<double>(zu[al]) * static_cast<double>(yu[al]);
+    }
+  }
+  __shared__ double sh[2][32];
+  for (int off = 16; off > 0; off >>= 1) {
+    e_can += __shfl_xor_sync(0xffffffffu, e_can, off);
+    e_frag += __shfl_xor_sync(0xffffffffu, e_frag, off);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) {
+    sh[0][w] = e_can;
+    sh[1][w] = e_frag;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
+      s0 += sh[0][q];
+      s1 += sh[1][q];
+    }
+    out[2 * blk_id] = -s0 / 3.0;
+    out[2 * blk_id + 1] = -s1 / 3.0;
+  }
+}
+
 // Sum of the per-block partials in a fixed order: out[0] canonical, out[1] projected.
 __global__ void k_t_finish(const double* part, long long nblk, double* out) {
   __shared__ double sh[2][32];
@@ -181,19 +295,17 @@ __global__ void k_swap_outer_rows(const T* src, T* dst, int v, int o, int Kp, in
 
 }  // namespace
 
-// A packed operand restricted to a row range (FP64: pointer offset; BF16: the kernel needs the
-// full plane stride, so the GEMM gets the row offset explicitly).
-struct Sub {
-  const Packed* P;
-  int row0, rows;
-};
-
 int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   const long long oo = 1LL * o * o, vv = 1LL * v * v, ov = 1LL * o * v, ooo = oo * o;
   const bool bf = mixed;
   cudaMemsetAsync(dstatus, 0, 16 * 4, s);
   const double* t1 = xcur;
   const double* t2 = xcur + ov;
+  cudaEvent_t ev_call0, ev_call1;
+  cudaEventCreate(&ev_call0);
+  cudaEventCreate(&ev_call1);
+  cudaEventRecord(ev_call0, s);
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // around each chunk's contraction launches
 
   // ---- operands (packed once per call)
   std::vector<void*> mine;
@@ -224,6 +336,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   Packed T2x = mk(static_cast<int>(vv * o), o), T2y = mk(static_cast<int>(vv * o), o);
   Packed O1 = mk(static_cast<int>(v * oo), o), O1T = mk(static_cast<int>(v * oo), o);
   double* ovoo = static_cast<double*>(tmp_alloc(ooo * v * 8));
+  const double* dU = nlo > 0 ? U : nullptr;
   if (!X1.p || !X2.p || !Tv.p || !TvT.p || !T2x.p || !T2y.p || !O1.p || !O1T.p || !ovoo) {
     cleanup();
     set_error("lnocc_triples: device allocation failed (operands)");
@@ -267,6 +380,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     mixed = keep;
     const long long tot = static_cast<long long>(X2.rows) * X2.Kp * (bf ? 2 : 1);
     const int blocks = static_cast<int>(std::min<long long>((tot + 255) / 256, 152LL * 32));
+    count_launch();
     if (bf)
       k_swap_outer_rows<unsigned short><<<blocks, 256, 0, s>>>(static_cast<const unsigned short*>(X2.p),
                                                                  static_cast<unsigned short*>(X1.p), v, o, X2.Kp, 2);
@@ -275,7 +389,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
                                                        o, X2.Kp, 1);
   }
 
-  // ---- pairs b <= c
+  // ---- pairs b <= c, processed in chunks of P pairs; W chunk [P][v][o][o][o] (FP32 on the mixed path)
   std::vector<int> hb, hc;
   for (int c = 0; c < v; ++c)
     for (int b = 0; b <= c; ++b) {
@@ -287,11 +401,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   int* dpc = static_cast<int*>(tmp_alloc(npair * 4));
   double* tpart = static_cast<double*>(tmp_alloc(static_cast<size_t>(npair) * v * 2 * 8));
   const long long slot_stride = v * ooo;
-  const int P = static_cast<int>(std::max(1LL, std::min<long long>(npair, (1LL << 26) / slot_stride)));
-  double* W = static_cast<double*>(tmp_alloc(static_cast<size_t>(P) * slot_stride * 8));
-  double* dU = nullptr;
-  if (nlo > 0) dU = const_cast<double*>(U);
-  if (!dpb || !dpc || !tpart || !W) {
+  const size_t wsz = bf ? 4 : 8;
+  const int P = static_cast<int>(std::max(1LL, std::min<long long>(npair, (64LL << 20) / (slot_stride * wsz))));
+  void* W = tmp_alloc(static_cast<size_t>(P) * slot_stride * wsz);
+  constexpr int kCfg = 12;
+  BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * kCfg * npair));
+  std::vector<BatchEntry> hbat(static_cast<size_t>(kCfg) * npair);
+  if (!dpb || !dpc || !tpart || !W || !dbat) {
     cleanup();
     set_error("lnocc_triples: device allocation failed (W chunk)");
     return LNOCC_ENOMEM;
@@ -301,43 +417,108 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   cudaStreamSynchronize(s);
 
   const int o2 = static_cast<int>(oo);
+  auto omap = [&](long long sm1, long long sm0, long long sn1, long long sn0, int mdiv, int ndiv, double beta) {
+    OutMap m{bf ? nullptr : static_cast<double*>(W), sm1, sm0, sn1, sn0, mdiv, ndiv, 1.0, beta};
+    if (bf) m.dst32 = static_cast<float*>(W);
+    return m;
+  };
+  // the twelve contractions: A, B, rows of A per pair, N, K, output map
+  struct Cfg {
+    const Packed* A;
+    const Packed* B;
+    int N, K;
+    OutMap C;
+  };
+  const Cfg cfg[kCfg] = {
+      {&X1, &Tv, o2, v, omap(ooo, oo, 1, o, o, o, 0.0)},    // G_i: (ai|bd) t_kj^cd
+      {&X1, &TvT, o2, v, omap(ooo, oo, 1, o, o, o, 1.0)},   // G_i: (ai|cd) t_jk^bd
+      {&T2x, &O1, o2, o, omap(ooo, oo, 1, o, o, o, 1.0)},   // G_i: -t_il^ab (ck|jl)
+      {&T2x, &O1T, o2, o, omap(ooo, oo, 1, o, o, o, 1.0)},  // G_i: -t_il^ac (bj|kl)
+      {&X2, &Tv, o2, v, omap(ooo, o, 1, oo, o, o, 1.0)},    // G_j: (bj|ad) t_ki^cd
+      {&T2y, &O1, o2, o, omap(ooo, o, 1, oo, o, o, 1.0)},   // G_j: -t_jl^ba (ck|il)
+      {&X2, &Tv, o2, v, omap(ooo, 1, o, oo, o, o, 1.0)},    // G_k: (ck|ad) t_ji^bd
+      {&T2y, &O1, o2, o, omap(ooo, 1, o, oo, o, o, 1.0)},   // G_k: -t_kl^ca (bj|il)
+      {&Tv, &X1, o, v, omap(oo, 1, 0, o, o, 1 << 30, 1.0)}, // G_4: t_ik^ad (bj|cd)
+      {&O1, &T2x, o, o, omap(oo, 1, 0, o, o, 1 << 30, 1.0)},// G_4: -(ai|kl) t_jl^bc
+      {&Tv, &X1, o, v, omap(oo, o, 0, 1, o, 1 << 30, 1.0)}, // G_6: t_ij^ad (ck|bd)
+      {&O1, &T2x, o, o, omap(oo, o, 0, 1, o, 1 << 30, 1.0)},// G_6: -(ai|jl) t_kl^cb
+  };
+  const bool staged = 2LL * ooo * wsz + (3LL * oo + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
+  const size_t esmem = 2 * ooo * wsz + (3 * oo + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
+  if (staged) {
+    if (bf)
+      cudaFuncSetAttribute(k_t_energy_staged<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(esmem));
+    else
+      cudaFuncSetAttribute(k_t_energy_staged<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(esmem));
+  }
+  double* Wd = static_cast<double*>(W);
+  // per-pair row offsets of every contraction, uploaded once: entry [g][pair]
+  for (int p = 0; p < npair; ++p) {
+    const int b = hb[p], c = hc[p];
+    const int xb = b * v * o, xc = c * v * o;
+    const int Ma = (b + 1) * o, Ma2 = (b + 1) * o2;
+    const long long cb = static_cast<long long>(p % P) * slot_stride;
+    const int rows[kCfg][3] = {{xb, c * o2, Ma},     {xc, b * o2, Ma},     {xb, c * o2, Ma},     {xc, b * o2, Ma},
+                               {xb, c * o2, Ma},     {xb, c * o2, Ma},     {xc, b * o2, Ma},     {xc, b * o2, Ma},
+                               {0, xc + b * o, Ma2}, {0, xc + b * o, Ma2}, {0, xb + c * o, Ma2}, {0, xb + c * o, Ma2}};
+    for (int g = 0; g < kCfg; ++g)
+      hbat[static_cast<size_t>(g) * npair + p] = BatchEntry{rows[g][0], rows[g][1], rows[g][2], 0, cb};
+  }
+  cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
   for (int p0 = 0; p0 < npair; p0 += P) {
     const int np = std::min(P, npair - p0);
-    for (int q = 0; q < np; ++q) {
-      const int b = hb[p0 + q], c = hc[p0 + q];
-      double* Wz = W + q * slot_stride;
-      const int Ma = (b + 1) * o;        // rows (a <= b, p)
-      const int Ma2 = (b + 1) * o2;      // rows (a <= b, p, q)
-      const int xb = b * v * o, xc = c * v * o;  // row offsets of the y = b / y = c slices of X1, X2, T2x, T2y
-      // G_i: rows (a,i), cols (k,j)  -> W[a][i][j][k]
-      const OutMap Gi{Wz, ooo, oo, 1, o, o, o, 1.0, 0.0};
-      OutMap Gi1 = Gi;
-      Gi1.beta = 1.0;
-      gemm_off(X1, xb, Tv, c * o2, Ma, o2, v, Gi, s, dstatus);
-      gemm_off(X1, xc, TvT, b * o2, Ma, o2, v, Gi1, s, dstatus);
-      gemm_off(T2x, xb, O1, c * o2, Ma, o2, o, Gi1, s, dstatus);
-      gemm_off(T2x, xc, O1T, b * o2, Ma, o2, o, Gi1, s, dstatus);
-      // G_j: rows (a,j), cols (k,i)
-      const OutMap Gj{Wz, ooo, o, 1, oo, o, o, 1.0, 1.0};
-      gemm_off(X2, xb, Tv, c * o2, Ma, o2, v, Gj, s, dstatus);
-      gemm_off(T2y, xb, O1, c * o2, Ma, o2, o, Gj, s, dstatus);
-      // G_k: rows (a,k), cols (j,i)
-      const OutMap Gk{Wz, ooo, 1, o, oo, o, o, 1.0, 1.0};
-      gemm_off(X2, xc, Tv, b * o2, Ma, o2, v, Gk, s, dstatus);
-      gemm_off(T2y, xc, O1, b * o2, Ma, o2, o, Gk, s, dstatus);
-      // G_4: rows (a,i,k), cols j ; G_6: rows (a,i,j), cols k
-      const OutMap G4{Wz, oo, 1, 0, o, o, 1 << 30, 1.0, 1.0};
-      const OutMap G6{Wz, oo, o, 0, 1, o, 1 << 30, 1.0, 1.0};
-      gemm_off(Tv, 0, X1, xc + b * o, Ma2, o, v, G4, s, dstatus);
-      gemm_off(O1, 0, T2x, xc + b * o, Ma2, o, o, G4, s, dstatus);
-      gemm_off(Tv, 0, X1, xb + c * o, Ma2, o, v, G6, s, dstatus);
-      gemm_off(O1, 0, T2x, xb + c * o, Ma2, o, o, G6, s, dstatus);
+    int maxb = 0;
+    for (int q = 0; q < np; ++q) maxb = std::max(maxb, hb[p0 + q]);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    for (int g = 0; g < kCfg; ++g) {
+      const int maxM = (g < 8) ? (maxb + 1) * o : (maxb + 1) * o2;
+      gemm_batched(*cfg[g].A, *cfg[g].B, dbat + static_cast<size_t>(g) * npair + p0, np, maxM, cfg[g].N, cfg[g].K,
+                   cfg[g].C, s, dstatus);
     }
-    k_t_energy<<<dim3(v, np), 128, 0, s>>>(W, slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
+    cudaEventRecord(e1, s);
+    gev.emplace_back(e0, e1);
+    if (staged) {
+      count_launch();
+      if (bf)
+        k_t_energy_staged<float, float><<<dim3(v, np), 256, esmem, s>>>(
+            static_cast<const float*>(W), slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
+      else
+        k_t_energy_staged<double, double><<<dim3(v, np), 256, esmem, s>>>(
+            Wd, slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
+    } else {
+      if (bf) {
+        set_error("lnocc_triples: nocc too large for the staged (T) energy kernel in this build");
+        cleanup();
+        return LNOCC_EINVAL;
+      }
+      count_launch();
+      k_t_energy<<<dim3(v, np), 128, 0, s>>>(Wd, slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
+    }
   }
+  count_launch();
   k_t_finish<<<1, 1024, 0, s>>>(tpart, 1LL * npair * v, scal + 4);
   cudaMemcpyAsync(h_scal + 4, scal + 4, 16, cudaMemcpyDeviceToHost, s);
+  cudaEventRecord(ev_call1, s);
   cudaStreamSynchronize(s);
+  {
+    float ms = 0.f;
+    t_gemm_ms = 0.0;
+    for (auto& pr : gev) {
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      t_gemm_ms += ms;
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    cudaEventElapsedTime(&ms, ev_call0, ev_call1);
+    t_triples_ms = ms;
+    cudaEventDestroy(ev_call0);
+    cudaEventDestroy(ev_call1);
+  }
   const int st = check_device();
   if (e_full) *e_full = h_scal[4];
   if (e_frag) *e_frag = nlo > 0 ? h_scal[5] : 0.0;

@@ -35,7 +35,9 @@ class Info(ctypes.Structure):
                 ("n_iter", ctypes.c_int), ("converged", ctypes.c_int), ("e_mp2", ctypes.c_double),
                 ("e_ccsd", ctypes.c_double), ("last_rms", ctypes.c_double), ("model_flops_ccsd", ctypes.c_double),
                 ("model_flops_t", ctypes.c_double), ("exec_flops", ctypes.c_double),
-                ("gemm_launches", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong)]
+                ("gemm_launches", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong), ("t_triples_gemm_ms", ctypes.c_double),
+                ("t_triples_ms", ctypes.c_double)]
 
 
 class LnoccError(RuntimeError):

@@ -1,0 +1,204 @@
+"""GPU parity: liblnocc (through the C-ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: every energy (MP2, CCSD, (T), and their fragment projections) within 1e-6 Eh of the
+oracle on the mixed BF16x3 path; the plain FP64 GPU path within 1e-9 Eh (CCSD convergence noise).
+Oracle values are either computed here (sizes the oracle finishes in seconds) or read from
+tests/golden/*.json, which tests/golden/make_golden.py writes from `oracle/` only.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ccsd as occ
+from oracle import fragment as ofr
+from oracle import triples as otr
+from paper_2407_11258_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MIXED_TOL = 1e-6
+FP64_TOL = 1e-9
+ENERGIES = ("e_mp2", "e_ccsd", "e_mp2_frag", "e_ccsd_frag", "e_t", "e_t_frag")
+
+
+@pytest.fixture(scope="module")
+def lnocc():
+    from paper_2407_11258_gb300 import build
+    from paper_2407_11258_gb300 import lnocc as m
+    build.build()
+    m.load()
+    return m
+
+
+def gpu_solve(lnocc, fr, prec, do_t=True, **opt):
+    dev = "cuda"
+    eps = torch.tensor(fr.eps, device=dev)
+    B = torch.tensor(fr.B, device=dev)
+    U = torch.tensor(fr.U_frag, device=dev)
+    opts = lnocc.default_opts(precision=prec, **opt)
+    f = lnocc.lnocc_build_ints(fr.nocc, fr.nvir, fr.naux, eps, B, opts)
+    try:
+        e, it, st = lnocc.lnocc_ccsd(f)
+        ec, em = lnocc.lnocc_fragment_energy(f, U)
+        info = f.info()
+        out = dict(e_mp2=info.e_mp2, e_ccsd=e, n_iter=it, e_ccsd_frag=ec, e_mp2_frag=em)
+        if do_t:
+            et, etf = lnocc.lnocc_triples(f, U)
+            out.update(e_t=et, e_t_frag=etf)
+        return out
+    finally:
+        f.free()
+
+
+def oracle_solve(fr, do_t=True):
+    r = occ.ccsd(fr.eps, fr.B, fr.nocc, tol_t=1e-10, tol_e=1e-12)
+    Ec = occ.pair_energy_matrix(r["t1"], r["t2"], fr.B, fr.nocc)
+    Em = occ.pair_energy_matrix(np.zeros_like(r["t1"]), occ.mp2_amplitudes(fr.eps, fr.B, fr.nocc), fr.B, fr.nocc)
+    out = dict(e_mp2=r["e_mp2"], e_ccsd=r["e_corr"], e_ccsd_frag=ofr.project(Ec, fr.U_frag),
+               e_mp2_frag=ofr.project(Em, fr.U_frag))
+    if do_t:
+        Et = otr.pair_matrix(r["t1"], r["t2"], fr.eps, fr.B, fr.nocc)
+        out.update(e_t=float(np.trace(Et)), e_t_frag=ofr.project(Et, fr.U_frag))
+    return out
+
+
+def assert_parity(got, ref, tol):
+    bad = {k: got[k] - ref[k] for k in ENERGIES if k in got and k in ref and not abs(got[k] - ref[k]) <= tol}
+    assert not bad, f"|dE| > {tol}: {bad}"
+
+
+def golden(name):
+    path = os.path.join(HERE, "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    return json.load(open(path))
+
+
+# ------------------------------------------------------------------ contraction engine
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 3e-5)])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 32, 64), (300, 77, 131), (137, 145, 2000), (16, 16, 921600 // 64),
+                                   (5000, 136, 3000), (257, 300, 65)])
+def test_contraction_engine(lnocc, prec, tol, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64)
+    B = torch.randn(N, K, generator=g, dtype=torch.float64)
+    C = torch.zeros(M, N, dtype=torch.float64, device="cuda")
+    lnocc.lnocc_debug_gemm(prec, A.cuda(), B.cuda(), C)
+    ref = A @ B.T
+    scale = (A.abs() @ B.abs().T).max()
+    assert ((C.cpu() - ref).abs().max() / scale).item() < tol
+
+
+# ------------------------------------------------------------------ small fragments
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_single_fragment_nocc4_nvir24(lnocc, prec, tol):
+    ref = golden("oracle_small.json")["single_fp64"]
+    got = gpu_solve(lnocc, synth.single_fp64(), prec)
+    assert_parity(got, ref, tol)
+
+
+@pytest.mark.parametrize("shape", [(6, 37, 150), (9, 70, 280), (3, 131, 140)])
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_ragged_fragments_against_live_oracle(lnocc, shape, prec, tol):
+    """Sizes that span several 128-row tiles and leave ragged tails in every GEMM dimension."""
+    o, v, q = shape
+    fr = synth.make_fragment(o, v, q, 500 + o + v, decay=20.0, frag=(0, 1) if o > 1 else (0,))
+    ref = oracle_solve(fr)
+    got = gpu_solve(lnocc, fr, prec)
+    assert_parity(got, ref, tol)
+
+
+def test_triples_scaled_nocc12_nvir96(lnocc):
+    ref = golden("oracle_small.json")["triples_scaled"]
+    for prec, tol in ((1, MIXED_TOL), (0, FP64_TOL)):
+        got = gpu_solve(lnocc, synth.triples_large(scaled=True), prec)
+        assert_parity(got, ref, tol)
+
+
+def test_uneven_batch_subset(lnocc):
+    """16 shrunk fragments of the uneven batch (gapped and small-gap), mixed precision."""
+    ref = golden("oracle_small.json")["batch_shrunk"]
+    shrink = lambda o, v: (max(2, o // 3), max(8, v // 10))  # noqa: E731
+    for f, r in enumerate(ref):
+        fr = synth.batch_fragment(f, scale_shape=shrink)
+        assert (fr.nocc, fr.nvir, fr.naux) == (r["nocc"], r["nvir"], r["naux"])
+        got = gpu_solve(lnocc, fr, 1, max_iter=300)
+        assert_parity(got, r, MIXED_TOL)
+
+
+# ------------------------------------------------------------------ full size
+
+def test_diamond_like_full_size(lnocc):
+    """nocc=16, nvir=240, naux=960: mixed path against the stored oracle energies."""
+    ref = golden("oracle_diamond.json")["diamond_like"]
+    got = gpu_solve(lnocc, synth.diamond_like(), 1)
+    assert_parity(got, ref, MIXED_TOL)
+
+
+# ------------------------------------------------------------------ properties
+
+def test_deterministic_repeat(lnocc):
+    fr = synth.make_fragment(5, 40, 160, 9, decay=20.0)
+    a = gpu_solve(lnocc, fr, 1)
+    b = gpu_solve(lnocc, fr, 1)
+    assert a == b
+
+
+def test_degenerate_rotation_invariance(lnocc):
+    """Rotating orbitals inside an exactly degenerate virtual pair keeps the Fock diagonal and the energy."""
+    fr = synth.make_fragment(4, 30, 120, 21, decay=20.0)
+    fr.eps[4 + 10] = fr.eps[4 + 11]
+    ref = gpu_solve(lnocc, fr, 0)
+    c, s = np.cos(0.6), np.sin(0.6)
+    R = np.eye(fr.nmo)
+    R[14:16, 14:16] = [[c, -s], [s, c]]
+    fr.B = np.einsum("pr,Qrs,qs->Qpq", R, fr.B, R)
+    rot = gpu_solve(lnocc, fr, 0)
+    for k in ENERGIES:
+        assert abs(rot[k] - ref[k]) < 1e-9, k
+
+
+def test_restart_from_converged_amplitudes(lnocc):
+    fr = synth.make_fragment(4, 30, 120, 31, decay=20.0)
+    eps, B = torch.tensor(fr.eps, device="cuda"), torch.tensor(fr.B, device="cuda")
+    f = lnocc.lnocc_build_ints(fr.nocc, fr.nvir, fr.naux, eps, B, lnocc.default_opts(precision=0))
+    t1 = torch.zeros(fr.nocc, fr.nvir, dtype=torch.float64, device="cuda")
+    t2 = torch.zeros(fr.nocc, fr.nocc, fr.nvir, fr.nvir, dtype=torch.float64, device="cuda")
+    e0, it0, _ = lnocc.lnocc_ccsd(f, t1_out=t1, t2_out=t2)
+    e1, it1, _ = lnocc.lnocc_ccsd(f, t1_in=t1, t2_in=t2, guess_mode=lnocc.LNOCC_GUESS_GIVEN)
+    assert it1 <= 3 < it0 and abs(e1 - e0) < 1e-10
+    assert torch.allclose(t2, t2.transpose(0, 1).transpose(2, 3), atol=1e-14)
+    f.free()
+
+
+def test_fault_paths(lnocc):
+    fr = synth.make_fragment(3, 20, 80, 41, decay=20.0)
+    eps, B = torch.tensor(fr.eps, device="cuda"), torch.tensor(fr.B, device="cuda")
+    # iteration cap -> ENOCONV with the last energy
+    f = lnocc.lnocc_build_ints(3, 20, 80, eps, B, lnocc.default_opts(precision=1, max_iter=2))
+    e, it, st = lnocc.lnocc_ccsd(f, allow_noconv=True)
+    assert st == lnocc.LNOCC_ENOCONV and it == 2 and np.isfinite(e)
+    f.free()
+    # NaN-poisoned integrals -> ENUMERIC
+    f = lnocc.lnocc_build_ints(3, 20, 80, eps, B, lnocc.default_opts(precision=1,
+                                                                      fault_inject=lnocc.LNOCC_FAULT_NAN_INPUT))
+    with pytest.raises(lnocc.LnoccError) as ei:
+        lnocc.lnocc_ccsd(f)
+    assert ei.value.code == lnocc.LNOCC_ENUMERIC
+    f.free()
+    # DIIS off reaches the same fixed point
+    a = gpu_solve(lnocc, fr, 0)
+    b = gpu_solve(lnocc, fr, 0, fault_inject=lnocc.LNOCC_FAULT_ZERO_DIIS, max_iter=300)
+    assert abs(a["e_ccsd"] - b["e_ccsd"]) < 1e-9
+    # occupied above virtual is rejected
+    bad = eps.clone()
+    bad[0] = 5.0
+    with pytest.raises(lnocc.LnoccError) as ei:
+        lnocc.lnocc_build_ints(3, 20, 80, bad, B, lnocc.default_opts())
+    assert ei.value.code == lnocc.LNOCC_ENUMERIC
