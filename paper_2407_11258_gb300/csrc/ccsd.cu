@@ -286,6 +286,11 @@ int Frag::build_consts(bool bf) {
   mixed = bf;  // contract_packed_b follows the operand precision
   c.Bp_t = alloc_packed(np_o, np_v, bf);
   c.Bm_t = alloc_packed(std::max(nm_o, 1), std::max(nm_v, 1), bf);
+  c.PBov = alloc_packed(static_cast<int>(ov), N, bf);
+  c.PBoo = alloc_packed(static_cast<int>(oo), N, bf);
+  c.PBvo = alloc_packed(static_cast<int>(ov), N, bf);
+  c.PBvv = alloc_packed(static_cast<int>(vv), N, bf);
+  if (c.PBov.p) pack(view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)), c.PBov, s);
   // (kc|ld) as rows (k,l), K (c,d)                       [Y_ij^kl]
   c.kl_cd = alloc_packed(static_cast<int>(oo), static_cast<int>(vv), bf);
   pack(view(ovov, kOne, A(o, ov * v), A(o, v), kOne, A(v, ov), A(v, 1)), c.kl_cd, s);
@@ -370,6 +375,14 @@ int Frag::check_device() {
   return LNOCC_OK;
 }
 
+void Frag::pack_df() {
+  const long long oo = 1LL * o * o, vv = 1LL * v * v, ov = 1LL * o * v;
+  Consts& c = C();
+  pack(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)), c.PBoo, s);
+  pack(view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)), c.PBvo, s);
+  pack(view(Bvv_h, kOne, kOne, A(static_cast<int>(vv), 1), kOne, kOne, A(N, vv)), c.PBvv, s);
+}
+
 // ------------------------------------------------------------------------------------------------
 // One CCSD residual + Jacobi update: reads t1 = x, t2 = x + ov; writes xnew (t + R/D) and enew (R/D).
 // Returns the rms of the update in *rms (device scalar scal[1]).
@@ -399,6 +412,8 @@ void Frag::iterate(bool fp64_residual) {
   contract(view(t1, kOne, kOne, A(v, 1), kOne, kOne, A(o, v)), view(Bov, kOne, A(N, ov), A(v, 1), kOne, kOne, A(o, v)),
            OutMap{Bvv_h, 0, v, vv, 1, 1 << 30, v, -1.0, 1.0});
 
+  pack_df();
+  const Consts& K = C();
   mark("dress");
   // ---- T1-transformed Fock matrix F^ = (1-T) h (1+T) + sum_Q [2 B^_Qpq x_Q - sum_k B^_Qpk B^_Qkq]
   launch_dress_mats(t1, Xm, Ym, o, v, s);
@@ -419,13 +434,13 @@ void Frag::iterate(bool fp64_residual) {
   {
     // oo: B^_oo[Q][p][k] B^_oo[Q][k][q]
     contract(view(Boo_h, kOne, kOne, A(o, o), kOne, A(N, oo), A(o, 1)),
-             view(Boo_h, kOne, kOne, A(o, 1), kOne, A(N, oo), A(o, o)), out_rowmajor(Fh, n, -1.0, 1.0), true);
+             view(Boo_h, kOne, kOne, A(o, 1), kOne, A(N, oo), A(o, o)), out_rowmajor(Fh, n, -1.0, 1.0));
     // ov: B^_oo[Q][p][k] B_ov[Q][k][c]
     contract(view(Boo_h, kOne, kOne, A(o, o), kOne, A(N, oo), A(o, 1)),
-             view(Bov, kOne, kOne, A(v, 1), kOne, A(N, ov), A(o, v)), out_rowmajor(Fh + o, n, -1.0, 1.0), true);
+             view(Bov, kOne, kOne, A(v, 1), kOne, A(N, ov), A(o, v)), out_rowmajor(Fh + o, n, -1.0, 1.0));
     // vo: B^_vo[Q][a][k] B^_oo[Q][k][i]
     contract(view(Bvo_h, kOne, kOne, A(v, o), kOne, A(N, ov), A(o, 1)),
-             view(Boo_h, kOne, kOne, A(o, 1), kOne, A(N, oo), A(o, o)), out_rowmajor(Fh + o * n, n, -1.0, 1.0), true);
+             view(Boo_h, kOne, kOne, A(o, 1), kOne, A(N, oo), A(o, o)), out_rowmajor(Fh + o * n, n, -1.0, 1.0));
     // vv: B^_vo[Q][a][k] B_ov[Q][k][c]
     contract(view(Bvo_h, kOne, kOne, A(v, o), kOne, A(N, ov), A(o, 1)),
              view(Bov, kOne, kOne, A(v, 1), kOne, A(N, ov), A(o, v)), out_rowmajor(Fh + o * n + o, n, -1.0, 1.0));
@@ -438,9 +453,8 @@ void Frag::iterate(bool fp64_residual) {
 
   mark("tau_u");
   // ---- Rsym = g^_aibj : (a,i) x (b,j) over Q, written to [i][j][a][b]
-  contract(view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
-           view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
-           OutMap{Rsym, v, o * vv, 1, vv, o, o, 1.0, 0.0});
+  gemm(K.PBvo, K.PBvo, static_cast<int>(ov), static_cast<int>(ov), N, OutMap{Rsym, v, o * vv, 1, vv, o, o, 1.0, 0.0},
+       s, dstatus);
   mark("g_aibj");
   // particle-particle ladder with the packed undressed integrals
   launch_ladder_ops(t2, C().Bp_t, C().Bm_t, o, v, s);
@@ -453,9 +467,8 @@ void Frag::iterate(bool fp64_residual) {
   // Wy[i][j][k][l] = Y_ij^kl = sum_cd (kc|ld) t_ij^cd ; Wb = g^_kilj + Y_ij^kl
   contract_packed_b(view(t2, kOne, kOne, A(static_cast<int>(oo), vv), kOne, kOne, A(static_cast<int>(vv), 1)),
                     C().kl_cd, static_cast<int>(oo), out_rowmajor(Wy, oo));
-  contract(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
-           view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
-           OutMap{Wb, o, oo * o, 1, oo, o, o, 1.0, 0.0});
+  gemm(K.PBoo, K.PBoo, static_cast<int>(oo), static_cast<int>(oo), N, OutMap{Wb, o, oo * o, 1, oo, o, o, 1.0, 0.0}, s,
+       dstatus);
   permute(view(Wy, kOne, kOne, A(static_cast<int>(oo), oo), kOne, kOne, A(static_cast<int>(oo), 1)), Wb, 1.0, s);
   mark("Y_Wb");
   // Rsym += sum_kl t_kl^ab Wb_ij^kl + sum_kl t_k^a t_l^b Y_ij^kl   (tau holds t1 (x) t1 here)
@@ -485,17 +498,19 @@ void Frag::iterate(bool fp64_residual) {
   mark("E2a");
   // Foo'_kj = F^_kj + sum_lcd u_lj^cd (kd|lc); S -= sum_k t_ik^ab Foo'_kj
   permute(view(Fh, kOne, kOne, A(o, n), kOne, kOne, A(o, 1)), Foo2, 0.0, s);
-  contract(view(ovov, kOne, kOne, A(o, ov * v), A(o, v), A(v, 1), A(v, ov)),
-           view(u, kOne, kOne, A(o, vv), A(o, o * vv), A(v, v), A(v, 1)),
-           out_rowmajor(Foo2, o, 1.0, 1.0), true);
+  // Mtmp[Q][d][i] = sum_kc B_Qkc u_ki^cd (shared with the singles term A1);
+  // sum_lcd u_lj^cd (kd|lc) = sum_{Q,d} B_Qkd Mtmp[Q][d][j]
+  contract(view(Bov, kOne, kOne, A(N, ov), kOne, kOne, A(static_cast<int>(ov), 1)),
+           view(u, kOne, A(v, 1), A(o, vv), kOne, A(o, o * vv), A(v, v)), out_rowmajor(Mtmp, ov));
+  contract(view(Bov, kOne, kOne, A(o, v), kOne, A(N, ov), A(v, 1)),
+           view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)), out_rowmajor(Foo2, o, 1.0, 1.0));
   mark("Foo");
   contract(view(t2, kOne, A(o, o * vv), A(static_cast<int>(vv), 1), kOne, kOne, A(o, vv)),
            view(Foo2, kOne, kOne, A(o, 1), kOne, kOne, A(o, o)), OutMap{S, o * vv, 1, 0, vv, static_cast<int>(vv),
                                                                        1 << 30, -1.0, 1.0});
   mark("E2b");
   // C2 intermediate X_kiac = g^_kiac - 1/2 sum_dl t_li^ad (kd|lc), stored [k][i][a][c]
-  contract(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
-           view(Bvv_h, kOne, kOne, A(static_cast<int>(vv), 1), kOne, kOne, A(N, vv)), out_rowmajor(Xk, vv));
+  gemm(K.PBoo, K.PBvv, static_cast<int>(oo), static_cast<int>(vv), N, out_rowmajor(Xk, vv), s, dstatus);
   contract_packed_b(view(t2, kOne, A(o, vv), A(v, v), kOne, A(o, o * vv), A(v, 1)), C().kc_ld, static_cast<int>(ov),
                     OutMap{Xk, vv, v, o * vv, 1, v, v, -0.5, 1.0});
   mark("X");
@@ -504,12 +519,10 @@ void Frag::iterate(bool fp64_residual) {
            view(Xk, kOne, A(o, vv), A(v, v), kOne, A(o, o * vv), A(v, 1)), out_rowmajor(Cp, ov));
   mark("Cp");
   // D2 intermediate Y[i][a][k][c] = 2 g^_aikc - g^_kiac + 1/2 sum_dl u_il^ad L_ldkc
-  contract(view(Bvo_h, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
-           view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
-           OutMap{Yk, ov, ovv, 0, 1, o, 1 << 30, 2.0, 0.0});
-  contract(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
-           view(Bvv_h, kOne, kOne, A(static_cast<int>(vv), 1), kOne, kOne, A(N, vv)),
-           OutMap{Yk, v, ovv, ov, 1, o, v, -1.0, 1.0});
+  gemm(K.PBvo, K.PBov, static_cast<int>(ov), static_cast<int>(ov), N, OutMap{Yk, ov, ovv, 0, 1, o, 1 << 30, 2.0, 0.0},
+       s, dstatus);
+  gemm(K.PBoo, K.PBvv, static_cast<int>(oo), static_cast<int>(vv), N, OutMap{Yk, v, ovv, ov, 1, o, v, -1.0, 1.0}, s,
+       dstatus);
   contract_packed_b(view(u, kOne, A(o, o * vv), A(v, v), kOne, A(o, vv), A(v, 1)), C().L, static_cast<int>(ov),
                     out_rowmajor(Yk, ov, 0.5, 1.0));
   mark("Yint");
@@ -520,23 +533,20 @@ void Frag::iterate(bool fp64_residual) {
 
   mark("D2");
   // ---- singles residual R1[i][a]
-  // A1 via DF: M[Q][d][i] = sum_kc B_Qkc u_ki^cd ; R1 += sum_{Q,d} B^_Qad M[Q][d][i]
-  contract(view(Bov, kOne, kOne, A(N, ov), kOne, kOne, A(static_cast<int>(ov), 1)),
-           view(u, kOne, A(v, 1), A(o, vv), kOne, A(o, o * vv), A(v, v)), out_rowmajor(Mtmp, ov));
+  // A1 via DF: R1 += sum_{Q,d} B^_Qad Mtmp[Q][d][i]
   contract(view(Bvv_h, kOne, kOne, A(v, v), kOne, A(N, vv), A(v, 1)),
            view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)), OutMap{R1, 0, 1, 0, v, 1 << 30, 1 << 30, 1.0, 0.0});
   mark("A1");
   // B1: R1 -= sum_klc u_kl^ac g^_kilc ; g^_kilc stored [i][k][l][c]
-  contract(view(Boo_h, kOne, kOne, A(static_cast<int>(oo), 1), kOne, kOne, A(N, oo)),
-           view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
-           OutMap{Gooov, ov, o * ov, 0, 1, o, 1 << 30, 1.0, 0.0});
+  gemm(K.PBoo, K.PBov, static_cast<int>(oo), static_cast<int>(ov), N, OutMap{Gooov, ov, o * ov, 0, 1, o, 1 << 30, 1.0, 0.0},
+       s, dstatus);
   contract(view(u, kOne, kOne, A(v, v), kOne, A(static_cast<int>(oo), vv), A(v, 1)),
            view(Gooov, kOne, kOne, A(o, o * ov), kOne, kOne, A(static_cast<int>(o * ov), 1)),
            OutMap{R1, 0, 1, 0, v, 1 << 30, 1 << 30, -1.0, 1.0});
   mark("B1");
   // C1: R1 += sum_kc u_ik^ac F^_kc
   contract(view(u, kOne, A(o, o * vv), A(v, v), kOne, A(o, vv), A(v, 1)),
-           view(Fh + o, kOne, kOne, A(1, 0), kOne, A(o, n), A(v, 1)), out_rowmajor(R1, 1, 1.0, 1.0), true);
+           view(Fh + o, kOne, kOne, A(1, 0), kOne, A(o, n), A(v, 1)), out_rowmajor(R1, 1, 1.0, 1.0));
 
   mark("C1");
   // ---- update: t2n = t2 + R/D, t1n = t1 + (R1 + F^_ai)/D1; rms of the update
@@ -579,6 +589,7 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
   n_iter = 0;
   const bool use_diis = dm > 0 && !(opts.fault_inject & LNOCC_FAULT_ZERO_DIIS);
   int nvec = 0, refine_left = mixed ? opts.n_refine : 0;
+  std::vector<double> hist_rms, hist_de;
   bool refining = false;
   const double tol_r = opts.conv_rms, tol_e = opts.conv_energy;
   for (int it = 1; it <= opts.max_iter; ++it) {
@@ -616,7 +627,23 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
       set_error("non-finite CCSD energy or residual");
       return LNOCC_ENUMERIC;
     }
-    const bool conv = rms < tol_r && std::fabs(e - e_old) < tol_e;
+    // Mixed residuals carry BF16x3 rounding noise: the update stalls at a noise floor (rms ~1e-10..1e-8,
+    // energy jitter ~1e-9..1e-8 Eh) instead of reaching the FP64 thresholds. There the energy test uses
+    // max(conv_energy, 1e-8), and a solve whose rms has stopped falling (no 20% drop over 4 iterations)
+    // while the energy moves by < 1e-7 is taken as converged at the noise floor.
+    const bool mixed_now = mixed && !refining;
+    const double te = mixed_now ? std::max(tol_e, 1e-8) : tol_e;
+    hist_rms.push_back(rms);
+    hist_de.push_back(std::fabs(e - e_old));
+    bool conv = rms < tol_r && std::fabs(e - e_old) < te;
+    if (mixed_now && !conv && hist_rms.size() >= 6) {
+      const size_t m = hist_rms.size();
+      const double best_before = *std::min_element(hist_rms.begin(), hist_rms.end() - 4);
+      const double best_recent = *std::min_element(hist_rms.end() - 4, hist_rms.end());
+      const double de_recent = *std::max_element(hist_de.end() - 4, hist_de.end());
+      conv = best_recent > 0.8 * best_before && de_recent < 1e-7 && rms < 1e-5;
+      (void)m;
+    }
     e_old = e;
     if (conv) {
       if (refine_left > 0) {  // switch to FP64 residuals for the last iterations
@@ -646,17 +673,15 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
 
 // Pair matrix E_ii' = sum_jab tau_ij^ab L[i'][j][a][b] (FP64), then the LO projection.
 int Frag::fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double* e_mp2_frag) {
-  const long long ov = 1LL * o * v, K = ov * o * v / o * o / o;  // o*v*v... (j,a,b) = o v^2
-  (void)K;
-  const int kk = o * v * v;
+  const long long ov = 1LL * o * v;
+  const long long kk = ov * v;  // (j,a,b)
   auto pair_and_project = [&](const double* t1, const double* t2, double* out_host) -> int {
     if (t1) {
       launch_tau(t1, t2, tau, o, v, s);
     } else {
       LN_CUDA(cudaMemcpyAsync(tau, t2, 1LL * o * o * v * v * 8, cudaMemcpyDeviceToDevice, s));
     }
-    contract(view(tau, kOne, kOne, A(o, kk), kOne, kOne, A(kk, 1)), view(Lpair, kOne, kOne, A(o, kk), kOne, kOne, A(kk, 1)),
-             out_rowmajor(Eii, o), true);
+    launch_pair_dots(tau, Lpair, o, kk, Eii, s);
     launch_project(Eii, U, o, nlo, scal + 2, s);
     LN_CUDA(cudaMemcpyAsync(h_scal + 2, scal + 2, 8, cudaMemcpyDeviceToHost, s));
     LN_CUDA(cudaStreamSynchronize(s));

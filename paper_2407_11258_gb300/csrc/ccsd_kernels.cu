@@ -274,6 +274,18 @@ __global__ void k_extrapolate(const double* vecs, const double* coef, int m, lon
   }
 }
 
+// E[i][i'] = sum_x tau[i][x] L[i'][x] over x = (j,a,b): one block per (i,i'), FP64, fixed order.
+__global__ void k_pair_dots(const double* __restrict__ tau, const double* __restrict__ L, int o, long long K,
+                            double* __restrict__ E) {
+  const int i = blockIdx.x / o, ip = blockIdx.x % o;
+  const double* a = tau + i * K;
+  const double* b = L + ip * K;
+  double acc = 0.0;
+  for (long long x = threadIdx.x; x < K; x += blockDim.x) acc += a[x] * b[x];
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) E[blockIdx.x] = t;
+}
+
 // E_frag = sum_alpha sum_ii' U[i][alpha] E[i][i'] U[i'][alpha]   (one block)
 __global__ void k_project(const double* E, const double* U, int o, int nlo, double* out) {
   double acc = 0.0;
@@ -445,6 +457,10 @@ void launch_extrapolate(const double* vecs, const double* coef, int m, long long
 void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s) {
   count_launch();
   k_project<<<1, 256, 0, s>>>(E, U, o, nlo, out);
+}
+void launch_pair_dots(const double* tau, const double* L, int o, long long K, double* E, cudaStream_t s) {
+  count_launch();
+  k_pair_dots<<<o * o, 512, 0, s>>>(tau, L, o, K, E);
 }
 void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s) {
   count_launch();

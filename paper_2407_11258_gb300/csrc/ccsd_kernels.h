@@ -23,6 +23,7 @@ void launch_diis_dots(const double* e_new, const double* e_all, long long len, i
 void launch_diis_solve(const double* G, int m, int mmax, int newest, double* coef, cudaStream_t s);
 void launch_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out, cudaStream_t s);
 void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s);
+void launch_pair_dots(const double* tau, const double* L, int o, long long K, double* E, cudaStream_t s);
 void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s);
 void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s);
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s);

@@ -19,6 +19,8 @@ struct Consts {
   Packed kb_cd;  // (kc|bd): rows (k,b), K (c,d)          -> Z_ij^kb
   Packed Vp, Vm; // packed (ac|bd) +- (ad|bc)             -> particle-particle ladder
   Packed Bp_t, Bm_t;  // per-iteration packed t+- operands of the ladder
+  Packed PBov;        // B_ov as rows (i,a), K = Q (constant)
+  Packed PBoo, PBvo, PBvv;  // per-iteration T1-transformed DF factors as rows (p,q), K = Q
   bool built = false;
 };
 
@@ -84,6 +86,7 @@ struct Frag {
   int check_device();
   void contract(const View& a, const View& b, const OutMap& c, bool force_fp64 = false);
   void contract_packed_b(const View& a, const Packed& PB, int N, const OutMap& c);
+  void pack_df();  // T1-transformed DF factors -> packed [pq][Q] operands of the current precision
   void iterate(bool fp64_residual);
   double energy_of(const double* x);
   int solve(int guess, const double* t1_in, const double* t2_in);

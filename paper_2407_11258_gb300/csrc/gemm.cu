@@ -29,34 +29,97 @@ long long& launch_counter() {
 // ------------------------------------------------------------------------------------------------
 // Packing
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ long long view_off(const View& v, long long r, int k) {
-  const long long r0 = r % v.R0, rr = r / v.R0;
-  const long long r1 = rr % v.R1, r2 = rr / v.R1;
+__device__ __forceinline__ long long view_roff(const View& v, int r) {
+  const int r0 = r % v.R0, rr = r / v.R0;
+  const int r1 = rr % v.R1, r2 = rr / v.R1;
+  return r2 * v.sr2 + r1 * v.sr1 + r0 * v.sr0;
+}
+__device__ __forceinline__ long long view_koff(const View& v, int k) {
   const int k0 = k % v.K0, kk = k / v.K0;
   const int k1 = kk % v.K1, k2 = kk / v.K1;
-  return r2 * v.sr2 + r1 * v.sr1 + r0 * v.sr0 + k2 * v.sk2 + k1 * v.sk1 + k0 * v.sk0;
+  return k2 * v.sk2 + k1 * v.sk1 + k0 * v.sk0;
+}
+__device__ __forceinline__ long long view_off(const View& v, long long r, int k) {
+  return view_roff(v, static_cast<int>(r)) + view_koff(v, k);
 }
 
+template <bool BF16>
+__device__ __forceinline__ void put(void* out, long long idx, long long plane, double x) {
+  if (BF16) {
+    __nv_bfloat16 hi, lo;
+    split_bf16(x, hi, lo);
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+    o[idx] = hi;
+    o[idx + plane] = lo;
+  } else {
+    static_cast<double*>(out)[idx] = x;
+  }
+}
+
+// Row-major pack (K index contiguous or nearly so in the source): one warp per (row, 256-wide K chunk).
 // Writes rows [0, rows(v)) of a packed operand at `out` (plane stride `plane` elements).
 template <bool BF16>
 __global__ void k_pack(View v, void* out, int Kp, long long plane) {
   const int K = v.K2 * v.K1 * v.K0;
-  const long long total = static_cast<long long>(v.R2) * v.R1 * v.R0 * Kp;
-  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int k = static_cast<int>(idx % Kp);
-    const long long r = idx / Kp;
-    double x = 0.0;
-    if (k < K) x = v.scale * v.src[view_off(v, r, k)];
-    if (BF16) {
-      __nv_bfloat16 hi, lo;
-      split_bf16(x, hi, lo);
-      __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
-      o[idx] = hi;
-      o[idx + plane] = lo;
-    } else {
-      static_cast<double*>(out)[idx] = x;
+  const int rows = v.R2 * v.R1 * v.R0;
+  const int lane = threadIdx.x % 32;
+  const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) / 32;
+  const long long nwarp = static_cast<long long>(gridDim.x) * blockDim.x / 32;
+  const int nchunk = (Kp + 255) / 256;
+  const long long items = static_cast<long long>(rows) * nchunk;
+  const bool kflat = (v.K1 == 1 && v.K2 == 1);
+  for (long long it = warp; it < items; it += nwarp) {
+    const int r = static_cast<int>(it / nchunk), ch = static_cast<int>(it % nchunk);
+    const double* src = v.src + view_roff(v, r);
+    const long long base = static_cast<long long>(r) * Kp;
+    const int kend = min(Kp, (ch + 1) * 256);
+    for (int k = ch * 256 + lane; k < kend; k += 32) {
+      double x = 0.0;
+      if (k < K) x = v.scale * src[kflat ? static_cast<long long>(k) * v.sk0 : view_koff(v, k)];
+      put<BF16>(out, base + k, plane, x);
     }
+  }
+}
+
+// Transposing pack for sources whose rows are contiguous (sr0 == 1) and K is strided:
+// 32 x 32 tiles through shared memory so that both the reads and the writes are coalesced.
+template <bool BF16>
+__global__ void k_pack_t(View v, void* out, int Kp, long long plane) {
+  __shared__ double tile[32][33];
+  const int K = v.K2 * v.K1 * v.K0;
+  const int rows = v.R2 * v.R1 * v.R0;
+  const int rb = blockIdx.x * 32, kb = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  for (int ky = ty; ky < 32; ky += 8) {
+    const int r = rb + tx, k = kb + ky;
+    double x = 0.0;
+    if (r < rows && k < K) x = v.scale * v.src[view_off(v, r, k)];
+    tile[ky][tx] = x;
+  }
+  __syncthreads();
+  for (int ry = ty; ry < 32; ry += 8) {
+    const int r = rb + ry, k = kb + tx;
+    if (r < rows && k < Kp) put<BF16>(out, static_cast<long long>(r) * Kp + k, plane, tile[tx][ry]);
+  }
+}
+
+static void launch_pack(const View& v, void* out, int Kp, long long plane, bool bf16, cudaStream_t s) {
+  const int rows = v.rows();
+  const bool transpose = v.sr0 == 1 && v.R0 >= 32 && (v.sk0 != 1);
+  count_launch();
+  if (transpose) {
+    dim3 grid((rows + 31) / 32, (Kp + 31) / 32);
+    if (bf16)
+      k_pack_t<true><<<grid, 256, 0, s>>>(v, out, Kp, plane);
+    else
+      k_pack_t<false><<<grid, 256, 0, s>>>(v, out, Kp, plane);
+  } else {
+    const long long items = static_cast<long long>(rows) * ((Kp + 255) / 256);
+    const int blocks = static_cast<int>(std::min<long long>((items + 7) / 8, 152LL * 32));
+    if (bf16)
+      k_pack<true><<<std::max(blocks, 1), 256, 0, s>>>(v, out, Kp, plane);
+    else
+      k_pack<false><<<std::max(blocks, 1), 256, 0, s>>>(v, out, Kp, plane);
   }
 }
 
@@ -64,27 +127,16 @@ void pack(const View& v, Packed& out, cudaStream_t s) {
   out.rows = v.rows();
   out.Kp = round_up(std::max(v.K(), 1), 64);
   const long long total = static_cast<long long>(out.rows) * out.Kp;
-  const int threads = 256;
-  const int blocks = static_cast<int>(std::min<long long>((total + threads - 1) / threads, 152LL * 32));
-  count_launch();
-  if (out.bf16)
-    k_pack<true><<<blocks, threads, 0, s>>>(v, out.p, out.Kp, total);
-  else
-    k_pack<false><<<blocks, threads, 0, s>>>(v, out.p, out.Kp, total);
+  launch_pack(v, out.p, out.Kp, total, out.bf16, s);
 }
 
 // Pack a view into rows [row0, row0 + v.rows()) of an existing packed operand `full`.
 void pack_rows(const View& v, Packed& full, int row0, cudaStream_t s) {
-  const long long total = static_cast<long long>(v.rows()) * full.Kp;
-  const int threads = 256;
-  const int blocks = static_cast<int>(std::min<long long>((total + threads - 1) / threads, 152LL * 32));
   const long long plane = static_cast<long long>(full.rows) * full.Kp;
   const size_t off = static_cast<size_t>(row0) * full.Kp;
-  count_launch();
-  if (full.bf16)
-    k_pack<true><<<blocks, threads, 0, s>>>(v, static_cast<__nv_bfloat16*>(full.p) + off, full.Kp, plane);
-  else
-    k_pack<false><<<blocks, threads, 0, s>>>(v, static_cast<double*>(full.p) + off, full.Kp, plane);
+  void* base = full.bf16 ? static_cast<void*>(static_cast<__nv_bfloat16*>(full.p) + off)
+                         : static_cast<void*>(static_cast<double*>(full.p) + off);
+  launch_pack(v, base, full.Kp, plane, full.bf16, s);
 }
 
 __global__ void k_permute(View v, double* dst, double beta) {
@@ -108,10 +160,18 @@ void permute(const View& v, double* dst, double beta, cudaStream_t s) {
   k_permute<<<blocks, threads, 0, s>>>(v, dst, beta);
 }
 
-__device__ __forceinline__ void store_out(const OutMap& C, int m, int n, double acc, long long base = 0) {
-  const long long off = base + static_cast<long long>(m / C.mdiv) * C.sm1 +
-                        static_cast<long long>(m % C.mdiv) * C.sm0 + static_cast<long long>(n / C.ndiv) * C.sn1 +
-                        static_cast<long long>(n % C.ndiv) * C.sn0;
+__device__ __forceinline__ long long out_moff(const OutMap& C, int m) {
+  const int m0 = m % C.mdiv, mm = m / C.mdiv;
+  const int m1 = mm % C.mdiv1, m2 = mm / C.mdiv1;
+  return m2 * C.sm2 + m1 * C.sm1 + static_cast<long long>(m0) * C.sm0;
+}
+__device__ __forceinline__ long long out_noff(const OutMap& C, int n) {
+  const int n0 = n % C.ndiv, nn = n / C.ndiv;
+  const int n1 = nn % C.ndiv1, n2 = nn / C.ndiv1;
+  return n2 * C.sn2 + n1 * C.sn1 + static_cast<long long>(n0) * C.sn0;
+}
+
+__device__ __forceinline__ void store_at(const OutMap& C, long long off, double acc) {
   if (C.dst32) {
     float r = static_cast<float>(C.alpha * acc);
     if (C.beta != 0.0) r += static_cast<float>(C.beta) * C.dst32[off];
@@ -123,23 +183,71 @@ __device__ __forceinline__ void store_out(const OutMap& C, int m, int n, double 
   }
 }
 
+// Epilogue store of an FP32 accumulator: the scaling is done in FP32 (alpha, beta are small exact
+// constants); an FP64 destination gets one FP64 add for beta = 1 and none for beta = 0.
+__device__ __forceinline__ void store_at_f(const OutMap& C, long long off, float v, float alpha, float beta) {
+  const float a = alpha * v;
+  if (C.dst32) {
+    C.dst32[off] = (beta != 0.f) ? fmaf(beta, C.dst32[off], a) : a;
+  } else {
+    double r = static_cast<double>(a);
+    if (C.beta == 1.0)
+      r += C.dst[off];
+    else if (C.beta != 0.0)
+      r += C.beta * C.dst[off];
+    C.dst[off] = r;
+  }
+}
+
+// Sixteen epilogue stores: all old values are loaded first (independent loads in flight together),
+// then combined and stored.
+__device__ __forceinline__ void store16(const OutMap& C, const long long (&off)[16], const bool (&ok)[16],
+                                        const float (&v)[16], float alpha, float beta) {
+  if (C.dst32) {
+    float old[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) old[j] = (beta != 0.f && ok[j]) ? C.dst32[off[j]] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (ok[j]) C.dst32[off[j]] = fmaf(beta, old[j], alpha * v[j]);
+  } else {
+    double old[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) old[j] = (C.beta != 0.0 && ok[j]) ? C.dst[off[j]] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (ok[j]) {
+        double r = static_cast<double>(alpha * v[j]);
+        if (C.beta == 1.0)
+          r += old[j];
+        else if (C.beta != 0.0)
+          r += C.beta * old[j];
+        C.dst[off[j]] = r;
+      }
+  }
+}
+
+__device__ __forceinline__ void store_out(const OutMap& C, int m, int n, double acc, long long base = 0) {
+  store_at(C, base + out_moff(C, m) + out_noff(C, n), acc);
+}
+
 // ------------------------------------------------------------------------------------------------
 // FP64 SIMT GEMM: 64x64 tile, 16-wide K steps, 256 threads with 4x4 outputs each.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, const double* __restrict__ B,
                                                   int M, int N, int Kp, OutMap C, int ksplit, double* ws,
-                                                  const BatchEntry* __restrict__ batch) {
+                                                  const BatchEntry* __restrict__ batch, int seg) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
   long long cbase = 0;
   int kbeg = blockIdx.z * ksplit, kend = min(Kp, kbeg + ksplit);
   if (batch) {  // one problem per blockIdx.z; no split-K
     const BatchEntry be = batch[blockIdx.z];
     if (m0 >= be.M) return;
-    A += static_cast<long long>(be.a_row0) * Kp;
-    B += static_cast<long long>(be.b_row0) * Kp;
+    A += static_cast<long long>(seg ? be.a_row1 : be.a_row0) * Kp;
+    B += static_cast<long long>(seg ? be.b_row1 : be.b_row0) * Kp;
     M = be.M;
     cbase = be.cbase;
     kbeg = 0;
@@ -168,18 +276,39 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, 
     }
     __syncthreads();
   }
+  if (ws) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) ws[(static_cast<long long>(blockIdx.z) * M + m) * N + n] = acc[i][j];
+      }
+    return;
+  }
+  // load every old value first, then store (independent loads in flight together)
+  long long off[4][4];
+  double old[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-      if (m < M && n < N) {
-        if (ws)
-          ws[(static_cast<long long>(blockIdx.z) * M + m) * N + n] = acc[i][j];
-        else
-          store_out(C, m, n, acc[i][j], cbase);
-      }
+      off[i][j] = (m < M && n < N) ? cbase + out_moff(C, m) + out_noff(C, n) : -1;
+      old[i][j] = 0.0;
+      if (off[i][j] >= 0 && C.beta != 0.0) old[i][j] = C.dst32 ? C.dst32[off[i][j]] : C.dst[off[i][j]];
     }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (off[i][j] >= 0) {
+        const double r = C.alpha * acc[i][j] + C.beta * old[i][j];
+        if (C.dst32)
+          C.dst32[off[i][j]] = static_cast<float>(r);
+        else
+          C.dst[off[i][j]] = r;
+      }
 }
 
 // Fixed-order sum of split-K partials ws[split][M][N], then the OutMap store.
@@ -226,10 +355,10 @@ void gemm_f64(const Packed& A, const Packed& B, int M, int N, int K, const OutMa
   const int splits = choose_splits(tiles, nk16 / 4, static_cast<long long>(M) * N);
   const int per = splits > 1 ? ((nk16 + splits - 1) / splits) * 16 : A.Kp;
   const int nsplit = splits > 1 ? (A.Kp + per - 1) / per : 1;
-  dim3 grid((N + 63) / 64, (M + 63) / 64, nsplit);
+  dim3 grid((M + 63) / 64, (N + 63) / 64, nsplit);
   count_launch();
   k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), M, N, A.Kp, C,
-                                  per, nsplit > 1 ? split_ws().p : nullptr, nullptr);
+                                  per, nsplit > 1 ? split_ws().p : nullptr, nullptr, 0);
   if (nsplit > 1) splitk_reduce(nsplit, M, N, C, s);
 }
 
@@ -246,50 +375,103 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGES = (200 * 1024) / STAGE_BYTES > 4 ? 4 : (200 * 1024) / STAGE_BYTES;
-  static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int EPI_BYTES = 4 * 32 * 17 * 4;  // epilogue transpose scratch (4 warps)
+  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 4 ? 4 : (192 * 1024) / STAGE_BYTES;
+  static constexpr int ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two accumulators: MMA of tile t+1 overlaps epilogue of t
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+// Arguments of one tcgen05 GEMM launch. Two K segments: C = A0 B0^T (nkb0 blocks) + A1 B1^T (nkb1 blocks)
+// accumulate into the same TMEM tile; rows of segment s start at a_row[s] / b_row[s] (or come from the
+// batch table, one problem per z). Split-K (kb_per < nkb0, ws != null) only with one segment.
+struct TcArgs {
+  int M, N, nkb0, nkb1;
+  int a_row0, b_row0, a_row1, b_row1;
+  int kb_per;
+  int tiles_m, tiles_n, tiles_z;
+  OutMap C;
+  float alpha_f, beta_f;  // FP32 copies of C.alpha / C.beta for the epilogue
+  int* status;
+  double* ws;
+  const BatchEntry* batch;
+};
+
+// Per-tile problem description, computed identically by every role.
+struct TileInfo {
+  bool valid;
+  int m0, n0, z, M, kb0, nkbA;
+  int a_row0, b_row0, a_row1, b_row1;
+  long long cbase;
 };
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M, int N,
-              int nkb_total, OutMap C, int* status, int a_row0, int b_row0, int kb_per, double* ws,
-              const BatchEntry* __restrict__ batch) {
-  using Cfg = TcCfg<BN>;
-  int kb0 = blockIdx.z * kb_per;
-  int nkb = min(nkb_total - kb0, kb_per);
-  long long cbase = 0;
-  if (batch) {  // one problem per blockIdx.z (rows [a_row0, a_row0 + M) of A); no split-K
-    const BatchEntry be = batch[blockIdx.z];
-    if (static_cast<int>(blockIdx.y) * Cfg::BM >= be.M) return;
-    a_row0 = be.a_row0;
-    b_row0 = be.b_row0;
-    M = be.M;
-    cbase = be.cbase;
-    kb0 = 0;
-    nkb = nkb_total;
+__device__ __forceinline__ TileInfo tile_info(const TcArgs& p, int t) {
+  TileInfo ti;
+  const int tm = t % p.tiles_m, tn = (t / p.tiles_m) % p.tiles_n, z = t / (p.tiles_m * p.tiles_n);
+  ti.m0 = tm * 128;
+  ti.n0 = tn * BN;
+  ti.z = z;
+  ti.M = p.M;
+  ti.a_row0 = p.a_row0;
+  ti.b_row0 = p.b_row0;
+  ti.a_row1 = p.a_row1;
+  ti.b_row1 = p.b_row1;
+  ti.cbase = 0;
+  ti.kb0 = z * p.kb_per;
+  ti.nkbA = min(p.nkb0 - ti.kb0, p.kb_per);
+  if (p.batch) {
+    const BatchEntry be = p.batch[z];
+    ti.M = be.M;
+    ti.a_row0 = be.a_row0;
+    ti.b_row0 = be.b_row0;
+    ti.a_row1 = be.a_row1;
+    ti.b_row1 = be.b_row1;
+    ti.cbase = be.cbase;
+    ti.kb0 = 0;
+    ti.nkbA = p.nkb0;
   }
+  ti.valid = ti.m0 < ti.M && ti.nkbA + p.nkb1 > 0;
+  return ti;
+}
+
+// Persistent warp-specialized GEMM: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
+// warp 2 = TMEM owner, warps 4..7 = epilogue (lanes 32*(w-4) .. +31 of the accumulator).
+template <int BN>
+__global__ void __launch_bounds__(256, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tB0,
+              const __grid_constant__ CUtensorMap tA1, const __grid_constant__ CUtensorMap tB1, const TcArgs p) {
+  using Cfg = TcCfg<BN>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::STAGE_BYTES);
+  float* epi = reinterpret_cast<float*>(smem + S * Cfg::STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::STAGE_BYTES + Cfg::EPI_BYTES);
   uint64_t* empty = full + S;
-  uint64_t* accf = empty + S;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* accf = empty + S;   // [2] MMA -> epilogue
+  uint64_t* acce = accf + 2;    // [2] epilogue -> MMA
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.y * Cfg::BM, n0 = blockIdx.x * BN;
+  const int ntiles = p.tiles_m * p.tiles_n * p.tiles_z;
+  const OutMap& C = p.C;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
     fence_barrier_init();
-    prefetch_tensormap(&tA);
-    prefetch_tensormap(&tB);
+    prefetch_tensormap(&tA0);
+    prefetch_tensormap(&tB0);
+    if (p.nkb1 > 0) {
+      prefetch_tensormap(&tA1);
+      prefetch_tensormap(&tB1);
+    }
   }
   if (warp == 2) tmem_alloc(tmem_holder, Cfg::TMEM_COLS);
   tc_fence_before();
@@ -299,84 +481,188 @@ __global__ void __launch_bounds__(128, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int issued = 0;
+    int g = 0;  // global K-block counter across tiles (stage / phase)
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (kb >= S && !mbar_wait(&empty[s], ((kb / S) - 1) & 1)) {
-        atomicExch(status, kDevTimeoutProducer);
-        ok = false;
-        break;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileInfo ti = tile_info<BN>(p, t);
+      if (!ti.valid) continue;
+      const int nkb = ti.nkbA + p.nkb1;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % S;
+        if (g >= S && !mbar_wait(&empty[s], ((g / S) - 1) & 1)) {
+          atomicExch(p.status, kDevTimeoutProducer);
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * Cfg::STAGE_BYTES;
+        mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
+        const bool seg0 = kb < ti.nkbA;
+        const CUtensorMap* ta = seg0 ? &tA0 : &tA1;
+        const CUtensorMap* tb = seg0 ? &tB0 : &tB1;
+        const int kc = (seg0 ? ti.kb0 + kb : kb - ti.nkbA) * Cfg::BK;
+        const int ar = (seg0 ? ti.a_row0 : ti.a_row1) + ti.m0, br = (seg0 ? ti.b_row0 : ti.b_row1) + ti.n0;
+        tma_load_3d(st, ta, &full[s], kc, ar, 0);
+        tma_load_3d(st + Cfg::A_BYTES, ta, &full[s], kc, ar, 1);
+        tma_load_3d(st + 2 * Cfg::A_BYTES, tb, &full[s], kc, br, 0);
+        tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, tb, &full[s], kc, br, 1);
       }
-      uint8_t* st = smem + s * Cfg::STAGE_BYTES;
-      mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-      const int kc = (kb0 + kb) * Cfg::BK;
-      tma_load_3d(st, &tA, &full[s], kc, a_row0 + m0, 0);
-      tma_load_3d(st + Cfg::A_BYTES, &tA, &full[s], kc, a_row0 + m0, 1);
-      tma_load_3d(st + 2 * Cfg::A_BYTES, &tB, &full[s], kc, b_row0 + n0, 0);
-      tma_load_3d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tB, &full[s], kc, b_row0 + n0, 1);
-      ++issued;
     }
-    if (!ok) {  // let the copies already in flight land before the CTA retires
-      for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1);
-    }
+    // let the copies in flight land before the CTA retires
+    for (int q = (g > S ? g - S : 0); q < g; ++q) mbar_wait(&full[q % S], (q / S) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16_f32(Cfg::BM, BN);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait(&full[s], (kb / S) & 1)) {
-        atomicExch(status, kDevTimeoutMma);
+    int g = 0, it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileInfo ti = tile_info<BN>(p, t);
+      if (!ti.valid) continue;
+      const int buf = it & 1;
+      if (it >= 2 && !mbar_wait(&acce[buf], ((it / 2) - 1) & 1)) {
+        atomicExch(p.status, kDevTimeoutMma);
         break;
       }
       tc_fence_after();
-      const uint32_t a_hi = smem_u32(smem + s * Cfg::STAGE_BYTES);
-      const uint32_t a_lo = a_hi + Cfg::A_BYTES;
-      const uint32_t b_hi = a_lo + Cfg::A_BYTES;
-      const uint32_t b_lo = b_hi + Cfg::B_BYTES;
+      const uint32_t acc = tmem + buf * Cfg::ACC_COLS;
+      const int nkb = ti.nkbA + p.nkb1;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % S;
+        if (!mbar_wait(&full[s], (g / S) & 1)) {
+          atomicExch(p.status, kDevTimeoutMma);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(smem + s * Cfg::STAGE_BYTES);
+        const uint32_t a_lo = a_hi + Cfg::A_BYTES;
+        const uint32_t b_hi = a_lo + Cfg::A_BYTES;
+        const uint32_t b_lo = b_hi + Cfg::B_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
-        const uint32_t off = kk * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
-        const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-        const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
-        mma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
-        mma_bf16(tmem, dah, dbl, idesc, 1u);
-        mma_bf16(tmem, dal, dbh, idesc, 1u);
+        for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
+          const uint32_t off = kk * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
+          const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+          const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
+          mma_bf16(acc, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
+          mma_bf16(acc, dah, dbl, idesc, 1u);
+          mma_bf16(acc, dal, dbh, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      mma_commit(&accf[buf]);
+      ++it;
     }
-    mma_commit(accf);
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: TMEM -> registers -> FP64 destination
-  if (!mbar_wait(accf, 0)) {
-    if (lane == 0) atomicExch(status, kDevTimeoutEpilogue);
-  } else {
-    tc_fence_after();
-    const int row = warp * 32 + lane;
-    const int m = m0 + row;
+  } else if (warp >= 4) {
+    // ---------------- epilogue warps
+    const int ew = warp - 4;  // TMEM lane quadrant
+    const bool colmajor = !p.ws && (C.sn0 == 1 || C.sn0 == -1);
+    float* tile = epi + ew * (32 * 17);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TileInfo ti = tile_info<BN>(p, t);
+      if (!ti.valid) continue;
+      const int buf = it & 1;
+      if (!mbar_wait(&accf[buf], (it / 2) & 1)) {
+        if (lane == 0) atomicExch(p.status, kDevTimeoutEpilogue);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t acc = tmem + buf * Cfg::ACC_COLS + (static_cast<uint32_t>(ew * 32) << 16);
+      const int M = ti.M;
+      if (p.ws) {  // split-K partials, FP64 row-major [z][M][N]
+        const int m = ti.m0 + ew * 32 + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-      if (m < M) {
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(acc + c0, v);
+          if (m < M)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < N) {
-            if (ws)
-              ws[(static_cast<long long>(blockIdx.z) * M + m) * N + n] = static_cast<double>(v[j]);
-            else
-              store_out(C, m, n, static_cast<double>(v[j]), cbase);
+            for (int j = 0; j < 16; ++j) {
+              const int n = ti.n0 + c0 + j;
+              if (n < p.N) p.ws[(static_cast<long long>(ti.z) * M + m) * p.N + n] = static_cast<double>(v[j]);
+            }
+        }
+      } else if (!colmajor) {
+        // one row per thread; column offsets advance incrementally (no division per element).
+        // Each 16-column chunk loads all old values before storing (independent loads, no aliasing stall).
+        const int m = ti.m0 + ew * 32 + lane;
+        const long long moff = ti.cbase + (m < M ? out_moff(C, m) : 0);
+        int n = ti.n0;
+        int d0 = n % C.ndiv, q = n / C.ndiv, d1 = q % C.ndiv1, d2 = q / C.ndiv1;
+        long long noff = d2 * C.sn2 + d1 * C.sn1 + static_cast<long long>(d0) * C.sn0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(acc + c0, v);
+          long long offs[16];
+          bool ok[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            offs[j] = moff + noff;
+            ok[j] = m < M && n < p.N;
+            ++n;
+            noff += C.sn0;
+            if (++d0 == C.ndiv) {
+              d0 = 0;
+              noff += C.sn1 - static_cast<long long>(C.ndiv) * C.sn0;
+              if (++d1 == C.ndiv1) {
+                d1 = 0;
+                noff += C.sn2 - static_cast<long long>(C.ndiv1) * C.sn1;
+              }
+            }
           }
+          store16(C, offs, ok, v, p.alpha_f, p.beta_f);
+        }
+      } else {
+        // columns contiguous in the destination: transpose 32 x 16 blocks through shared memory so that
+        // consecutive lanes store consecutive columns; row offsets computed once per tile
+        const int jl = lane % 16, rh = lane / 16;
+        long long moffs[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int m = ti.m0 + ew * 32 + rh + 2 * r;
+          moffs[r] = m < M ? ti.cbase + out_moff(C, m) : -1;
+        }
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(acc + c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tile[lane * 17 + j] = v[j];
+          __syncwarp();
+          const int n = ti.n0 + c0 + jl;
+          const long long noff = (n < p.N) ? out_noff(C, n) : 0;
+          long long offs[16];
+          bool ok[16];
+          float w[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            offs[r] = moffs[r] + noff;
+            ok[r] = moffs[r] >= 0 && n < p.N;
+            w[r] = tile[(rh + 2 * r) * 17 + jl];
+          }
+          store16(C, offs, ok, w, p.alpha_f, p.beta_f);
+          __syncwarp();
         }
       }
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);
+      ++it;
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 2) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
 }
 
 // ---- host side: tensor maps
@@ -413,92 +699,135 @@ static bool make_map(CUtensorMap* map, const Packed& P, int box_rows) {
 }
 
 template <int BN>
-static void launch_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,
-                      cudaStream_t s, int* dstatus) {
-  using Cfg = TcCfg<BN>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    attr = true;
+static void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+    done = true;
   }
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, A, Cfg::BM) || !make_map(&tb, B, BN)) {
-    set_error("cuTensorMapEncodeTiled failed");
-    return;
-  }
-  const long long tiles = static_cast<long long>((N + BN - 1) / BN) * ((M + Cfg::BM - 1) / Cfg::BM);
-  const int nkb = A.Kp / 64;
-  const int splits = choose_splits(tiles, nkb, static_cast<long long>(M) * N);
-  const int per = (nkb + splits - 1) / splits;
-  dim3 grid((N + BN - 1) / BN, (M + Cfg::BM - 1) / Cfg::BM, splits);
-  count_launch();
-  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM, s>>>(ta, tb, M, N, nkb, C, dstatus, a_row0, b_row0, per,
-                                              splits > 1 ? split_ws().p : nullptr, nullptr);
-  if (splits > 1) splitk_reduce(splits, M, N, C, s);
 }
 
+// One launch: segment 1 is used when A1 != nullptr.
 template <int BN>
-static void launch_tc_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N,
-                              const OutMap& C, cudaStream_t s, int* dstatus) {
+static void launch_tc(const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1, TcArgs args,
+                      int gridM, int nbatch, cudaStream_t s) {
   using Cfg = TcCfg<BN>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    attr = true;
-  }
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, A, Cfg::BM) || !make_map(&tb, B, BN)) {
+  set_smem_attr<BN>();
+  CUtensorMap ta0, tb0, ta1, tb1;
+  if (!make_map(&ta0, A0, Cfg::BM) || !make_map(&tb0, B0, BN) ||
+      (A1 && (!make_map(&ta1, *A1, Cfg::BM) || !make_map(&tb1, *B1, BN)))) {
     set_error("cuTensorMapEncodeTiled failed");
     return;
   }
-  dim3 grid((N + BN - 1) / BN, (maxM + Cfg::BM - 1) / Cfg::BM, nbatch);
+  if (!A1) {
+    ta1 = ta0;
+    tb1 = tb0;
+  }
+  int splits = 1;
+  if (!A1 && !args.batch) {
+    const long long tiles = static_cast<long long>((args.N + BN - 1) / BN) * gridM;
+    splits = choose_splits(tiles, args.nkb0, static_cast<long long>(args.M) * args.N);
+  }
+  args.kb_per = (args.nkb0 + splits - 1) / splits;
+  args.ws = splits > 1 ? split_ws().p : nullptr;
+  args.tiles_m = gridM;
+  args.tiles_n = (args.N + BN - 1) / BN;
+  args.tiles_z = args.batch ? nbatch : splits;
+  args.alpha_f = static_cast<float>(args.C.alpha);
+  args.beta_f = static_cast<float>(args.C.beta);
+  const long long ntiles = static_cast<long long>(args.tiles_m) * args.tiles_n * args.tiles_z;
+  const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   count_launch();
-  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM, s>>>(ta, tb, maxM, N, A.Kp / 64, C, dstatus, 0, 0, A.Kp / 64, nullptr,
-                                              dbatch);
+  k_gemm_tc<BN><<<grid, 256, Cfg::SMEM, s>>>(ta0, tb0, ta1, tb1, args);
+  if (splits > 1) splitk_reduce(splits, args.M, args.N, args.C, s);
 }
 
-void gemm_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N, int K,
-                  const OutMap& C, cudaStream_t s, int* dstatus) {
-  if (nbatch <= 0 || maxM <= 0 || N <= 0) return;
-  GemmStats& st = gemm_stats();
-  st.launches++;
-  st.flops += 2.0 * maxM * N * K * nbatch * 0.5;  // rows shrink along the batch; counted as half
-  if (A.bf16) {
-    if (N <= 32)
-      launch_tc_batched<32>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
-    else if (N <= 64)
-      launch_tc_batched<64>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
-    else if (N <= 128)
-      launch_tc_batched<128>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
-    else if (N <= 144)
-      launch_tc_batched<144>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
-    else if (N <= 192)
-      launch_tc_batched<192>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
-    else
-      launch_tc_batched<256>(A, B, dbatch, nbatch, maxM, N, C, s, dstatus);
-  } else {
-    dim3 grid((N + 63) / 64, (maxM + 63) / 64, nbatch);
-    count_launch();
-    k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), maxM, N, A.Kp,
-                                    C, A.Kp, nullptr, dbatch);
-  }
+static void dispatch_tc(const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1, const TcArgs& a,
+                        int gridM, int nbatch, cudaStream_t s) {
+  const int N = a.N;
+  if (N <= 32)
+    launch_tc<32>(A0, B0, A1, B1, a, gridM, nbatch, s);
+  else if (N <= 64)
+    launch_tc<64>(A0, B0, A1, B1, a, gridM, nbatch, s);
+  else if (N <= 128)
+    launch_tc<128>(A0, B0, A1, B1, a, gridM, nbatch, s);
+  else if (N <= 144)
+    launch_tc<144>(A0, B0, A1, B1, a, gridM, nbatch, s);
+  else if (N <= 192)
+    launch_tc<192>(A0, B0, A1, B1, a, gridM, nbatch, s);
+  else
+    launch_tc<256>(A0, B0, A1, B1, a, gridM, nbatch, s);
+}
+
+static TcArgs tc_args(int M, int N, int nkb0, int nkb1, const OutMap& C, int* dstatus) {
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.nkb0 = nkb0;
+  a.nkb1 = nkb1;
+  a.kb_per = nkb0;
+  a.C = C;
+  a.status = dstatus;
+  return a;
 }
 
 void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,
              cudaStream_t s, int* dstatus) {
-  // N tile: the smallest of {32, 64, 128, 144, 192, 256} that covers N (larger N tiles at 256)
-  if (N <= 32)
-    launch_tc<32>(A, a_row0, B, b_row0, M, N, C, s, dstatus);
-  else if (N <= 64)
-    launch_tc<64>(A, a_row0, B, b_row0, M, N, C, s, dstatus);
-  else if (N <= 128)
-    launch_tc<128>(A, a_row0, B, b_row0, M, N, C, s, dstatus);
-  else if (N <= 144)
-    launch_tc<144>(A, a_row0, B, b_row0, M, N, C, s, dstatus);
-  else if (N <= 192)
-    launch_tc<192>(A, a_row0, B, b_row0, M, N, C, s, dstatus);
-  else
-    launch_tc<256>(A, a_row0, B, b_row0, M, N, C, s, dstatus);
+  TcArgs a = tc_args(M, N, A.Kp / 64, 0, C, dstatus);
+  a.a_row0 = a_row0;
+  a.b_row0 = b_row0;
+  dispatch_tc(A, B, nullptr, nullptr, a, (M + 127) / 128, 1, s);
+}
+
+void gemm_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N, int K,
+                  const OutMap& C, cudaStream_t s, int* dstatus) {
+  gemm2_batched(A, B, nullptr, nullptr, dbatch, nbatch, maxM, N, K, 0, C, s, dstatus);
+}
+
+void gemm2_batched(const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1, const BatchEntry* dbatch,
+                   int nbatch, int maxM, int N, int K0, int K1, const OutMap& C, cudaStream_t s, int* dstatus) {
+  if (nbatch <= 0 || maxM <= 0 || N <= 0) return;
+  GemmStats& st = gemm_stats();
+  st.launches++;
+  st.flops += 2.0 * maxM * N * (K0 + K1) * nbatch * 0.5;  // rows shrink along the batch; counted as half
+  if (A0.bf16) {
+    TcArgs a = tc_args(maxM, N, A0.Kp / 64, A1 ? A1->Kp / 64 : 0, C, dstatus);
+    a.batch = dbatch;
+    dispatch_tc(A0, B0, A1, B1, a, (maxM + 127) / 128, nbatch, s);
+  } else {
+    dim3 grid((maxM + 63) / 64, (N + 63) / 64, nbatch);
+    count_launch();
+    k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A0.p), static_cast<const double*>(B0.p), maxM, N,
+                                    A0.Kp, C, A0.Kp, nullptr, dbatch, 0);
+    if (A1) {
+      OutMap C1 = C;
+      C1.beta = 1.0;
+      count_launch();
+      k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A1->p), static_cast<const double*>(B1->p), maxM, N,
+                                      A1->Kp, C1, A1->Kp, nullptr, dbatch, 1);
+    }
+  }
+}
+
+void gemm2_off(const Packed& A0, int a0, const Packed& B0, int b0, int K0, const Packed& A1, int a1, const Packed& B1,
+               int b1, int K1, int M, int N, const OutMap& C, cudaStream_t s, int* dstatus) {
+  if (M <= 0 || N <= 0) return;
+  GemmStats& st = gemm_stats();
+  st.launches++;
+  st.flops += 2.0 * M * N * (K0 + K1);
+  if (A0.bf16) {
+    TcArgs a = tc_args(M, N, A0.Kp / 64, A1.Kp / 64, C, dstatus);
+    a.a_row0 = a0;
+    a.b_row0 = b0;
+    a.a_row1 = a1;
+    a.b_row1 = b1;
+    dispatch_tc(A0, B0, &A1, &B1, a, (M + 127) / 128, 1, s);
+  } else {
+    gemm_off(A0, a0, B0, b0, M, N, K0, C, s, dstatus);
+    OutMap C1 = C;
+    C1.beta = 1.0;
+    gemm_off(A1, a1, B1, b1, M, N, K1, C1, s, dstatus);
+  }
 }
 
 void gemm_off(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, int K, const OutMap& C,

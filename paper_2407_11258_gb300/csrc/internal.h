@@ -18,9 +18,10 @@ enum DevErr : int {
   kDevBadShape = 4,
 };
 
-// Destination of a contraction: C(m, n) ->
-//   dst[(m / mdiv) * sm1 + (m % mdiv) * sm0 + (n / ndiv) * sn1 + (n % ndiv) * sn0]
-// and dst = alpha * C + beta * dst (beta = 0 overwrites).
+// Destination of a contraction: C(m, n) with m = (m2, m1, m0), n = (n2, n1, n0),
+//   m0 = m % mdiv, m1 = (m / mdiv) % mdiv1, m2 = m / (mdiv * mdiv1)   (same for n)
+//   dst[m2*sm2 + m1*sm1 + m0*sm0 + n2*sn2 + n1*sn1 + n0*sn0] = alpha * C + beta * dst (beta = 0 overwrites).
+// The two-level form {dst, sm1, sm0, sn1, sn0, mdiv, ndiv, alpha, beta} leaves the outer levels unused.
 // When dst32 is set the destination is FP32 instead (dst unused).
 struct OutMap {
   double* dst;
@@ -28,6 +29,8 @@ struct OutMap {
   int mdiv, ndiv;
   double alpha, beta;
   float* dst32 = nullptr;
+  long long sm2 = 0, sn2 = 0;
+  int mdiv1 = 1 << 30, ndiv1 = 1 << 30;
 };
 
 inline OutMap out_rowmajor(double* dst, long long ldc, double alpha = 1.0, double beta = 0.0) {
@@ -37,7 +40,7 @@ inline OutMap out_rowmajor(double* dst, long long ldc, double alpha = 1.0, doubl
 // One problem of a batched GEMM: rows [a_row0, a_row0 + M) of A against rows [b_row0, b_row0 + N) of B,
 // destination offset cbase (elements) added to the OutMap.
 struct BatchEntry {
-  int a_row0, b_row0, M, pad;
+  int a_row0, b_row0, M, a_row1, b_row1, pad;
   long long cbase;
 };
 
@@ -85,6 +88,11 @@ void gemm_off(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, i
               cudaStream_t s, int* dstatus);
 void gemm_batched(const Packed& A, const Packed& B, const BatchEntry* dbatch, int nbatch, int maxM, int N, int K,
                   const OutMap& C, cudaStream_t s, int* dstatus);
+// Two K segments accumulated in one pass: C = A0 B0^T (K0) + A1 B1^T (K1); batched rows from the table.
+void gemm2_batched(const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1, const BatchEntry* dbatch,
+                   int nbatch, int maxM, int N, int K0, int K1, const OutMap& C, cudaStream_t s, int* dstatus);
+void gemm2_off(const Packed& A0, int a0, const Packed& B0, int b0, int K0, const Packed& A1, int a1, const Packed& B1,
+               int b1, int K1, int M, int N, const OutMap& C, cudaStream_t s, int* dstatus);
 // dispatch on A.bf16
 void gemm(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s,
           int* dstatus);

@@ -8,8 +8,9 @@
 // once (2 o^3 v^4 + 2 o^4 v^3 flops in the contractions), and the projection over (i, i') stays
 // local to the block.
 //
-// For a fixed (b, c) the six d-terms and six l-terms of W are GEMMs over d (or l) whose rows run
-// over a and one occupied index:
+// Within a slab of fixed b (virtual c >= b in chunks that fit the L2, a <= b) each of the six
+// permutation terms is one GEMM whose d-part (K = v) and l-part (K = o) accumulate in the same
+// tensor-memory tile (listed per fixed (b, c); rows run over a and one or two occupied indices):
 //   G_i  rows (a,i), cols (k,j): (ai|bd) t_kj^cd + (ai|cd) t_jk^bd - t_il^ab (ck|jl) - t_il^ac (bj|kl)
 //   G_j  rows (a,j), cols (k,i): (bj|ad) t_ki^cd - t_jl^ba (ck|il)
 //   G_k  rows (a,k), cols (j,i): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
@@ -39,27 +40,20 @@ __constant__ int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 
 
 // Block energy. One CTA per (pair, a) with a <= b; threads over (j, k).
 // W: [slot][a][i][j][k]; out: per block {canonical, projected} partials (FP64).
-__global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, const int* __restrict__ pb,
-                           const int* __restrict__ pc, int pair0, int o, int v, const double* __restrict__ eps,
-                           const double* __restrict__ t1, const double* __restrict__ ovov,
-                           const double* __restrict__ U, int nlo, double* __restrict__ out) {
+__global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
+                           const double* __restrict__ eps, const double* __restrict__ t1,
+                           const double* __restrict__ ovov, const double* __restrict__ U, int nlo,
+                           double* __restrict__ out) {
   const int slot = blockIdx.y;
   const int a = blockIdx.x;
-  const int b = pb[pair0 + slot], c = pc[pair0 + slot];
+  const int c = c0 + slot;
   const long long oblk = 1LL * o * o * o;
-  const long long blk_id = (1LL * (pair0 + slot)) * v + a;
-  if (a > b) {
-    if (threadIdx.x == 0) {
-      out[2 * blk_id] = 0.0;
-      out[2 * blk_id + 1] = 0.0;
-    }
-    return;
-  }
+  const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
   const double* Wb = W + slot * slot_stride + a * oblk;
   const int x[3] = {a, b, c};
   const double ex = eps[o + a] + eps[o + b] + eps[o + c];
   const long long ov = 1LL * o * v;
-  auto widx = [&](int y0, int y1, int y2) { return (1LL * y0 * o + y1) * o + y2; };
+  auto widx = [&](int y0, int y1, int y2) { return (1LL * y0 * o + y2) * o + y1; };  // W stored [a][i][k][j]
   // w and v of the block at occupied (y0, y1, y2)
   auto wv = [&](int y0, int y1, int y2, double& w, double& vv) {
     const double Wv = Wb[widx(y0, y1, y2)];
@@ -140,18 +134,14 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
 // (a sum of positive terms: no cancellation when it is rounded to Real). Threads then run over (j, k)
 // and every distinct ordering of (a, b, c); the i-sums are accumulated in Real and the block sum in FP64.
 template <typename TW, typename Real>
-__global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, const int* __restrict__ pb,
-                                  const int* __restrict__ pc, int pair0, int o, int v, const double* __restrict__ eps,
-                                  const double* __restrict__ t1, const double* __restrict__ ovov,
-                                  const double* __restrict__ U, int nlo, double* __restrict__ out) {
+__global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
+                                  const double* __restrict__ eps, const double* __restrict__ t1,
+                                  const double* __restrict__ ovov, const double* __restrict__ U, int nlo,
+                                  double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int slot = blockIdx.y, a = blockIdx.x;
-  const int b = pb[pair0 + slot], c = pc[pair0 + slot];
-  const long long blk_id = (1LL * (pair0 + slot)) * v + a;
-  if (a > b) {
-    if (threadIdx.x == 0) out[2 * blk_id] = out[2 * blk_id + 1] = 0.0;
-    return;
-  }
+  const int c = c0 + slot;
+  const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
   const int o2 = o * o, o3 = o2 * o;
   Real* sw = reinterpret_cast<Real*>(smraw);
   Real* sv = sw + o3;
@@ -182,7 +172,7 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   const TW* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
   for (int idx = threadIdx.x; idx < o3; idx += blockDim.x) {
     const int y0 = idx / o2, y1 = (idx / o) % o, y2 = idx % o;
-    const Real Wv = static_cast<Real>(Wb[idx]);
+    const Real Wv = static_cast<Real>(Wb[y0 * o2 + y2 * o + y1]);  // W stored [a][i][k][j]
     const Real disc = Sab[y0 * o + y1] * tc[y2] + Sac[y0 * o + y2] * tb[y1] + Sbc[y1 * o + y2] * ta[y0];
     const Real d = dm[y0] + dm[y1] + dm[y2];
     Real sc;
@@ -389,60 +379,46 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
                                                        o, X2.Kp, 1);
   }
 
-  // ---- pairs b <= c, processed in chunks of P pairs; W chunk [P][v][o][o][o] (FP32 on the mixed path)
-  std::vector<int> hb, hc;
-  for (int c = 0; c < v; ++c)
-    for (int b = 0; b <= c; ++b) {
-      hb.push_back(b);
-      hc.push_back(c);
-    }
-  const int npair = static_cast<int>(hb.size());
-  int* dpb = static_cast<int*>(tmp_alloc(npair * 4));
-  int* dpc = static_cast<int*>(tmp_alloc(npair * 4));
-  double* tpart = static_cast<double*>(tmp_alloc(static_cast<size_t>(npair) * v * 2 * 8));
-  const long long slot_stride = v * ooo;
+  // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
-  const int P = static_cast<int>(std::max(1LL, std::min<long long>(npair, (64LL << 20) / (slot_stride * wsz))));
-  void* W = tmp_alloc(static_cast<size_t>(P) * slot_stride * wsz);
-  constexpr int kCfg = 12;
-  BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * kCfg * npair));
-  std::vector<BatchEntry> hbat(static_cast<size_t>(kCfg) * npair);
-  if (!dpb || !dpc || !tpart || !W || !dbat) {
+  const long long welems = std::max<long long>((96LL << 20) / static_cast<long long>(wsz), v * ooo);
+  void* W = tmp_alloc(static_cast<size_t>(welems) * wsz);
+  long long nblk_total = 0;
+  for (int b = 0; b < v; ++b) nblk_total += 1LL * (b + 1) * (v - b);
+  double* tpart = static_cast<double*>(tmp_alloc(static_cast<size_t>(nblk_total) * 2 * 8));
+  // chunk plan and the per-c batch tables of the sigma2 / sigma5 terms (uploaded once)
+  struct Chunk {
+    int b, c0, nc;
+    long long tab, part;
+  };
+  std::vector<Chunk> plan;
+  std::vector<BatchEntry> hbat;
+  {
+    long long part = 0;
+    for (int b = 0; b < v; ++b) {
+      const long long slab = 1LL * (b + 1) * ooo;  // W elements per c
+      const int ncmax = static_cast<int>(std::max(1LL, welems / slab));
+      for (int c0 = b; c0 < v; c0 += ncmax) {
+        const int nc = std::min(ncmax, v - c0);
+        plan.push_back(Chunk{b, c0, nc, static_cast<long long>(hbat.size()), part});
+        const int Ma = (b + 1) * o;
+        for (int q = 0; q < nc; ++q) {
+          const int arow = (c0 + q) * v * o;           // rows (c, a, .) of X1 / T2x / X2 / T2y
+          const int brow = b * static_cast<int>(oo);  // rows (b, ., .) of TvT / O1T / Tv / O1
+          hbat.push_back(BatchEntry{arow, brow, Ma, arow, brow, 0, q * slab});
+        }
+        part += 1LL * (b + 1) * nc;
+      }
+    }
+  }
+  BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * std::max<size_t>(hbat.size(), 1)));
+  if (!W || !tpart || !dbat) {
     cleanup();
     set_error("lnocc_triples: device allocation failed (W chunk)");
     return LNOCC_ENOMEM;
   }
-  cudaMemcpyAsync(dpb, hb.data(), npair * 4, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(dpc, hc.data(), npair * 4, cudaMemcpyHostToDevice, s);
-  cudaStreamSynchronize(s);
+  cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
 
-  const int o2 = static_cast<int>(oo);
-  auto omap = [&](long long sm1, long long sm0, long long sn1, long long sn0, int mdiv, int ndiv, double beta) {
-    OutMap m{bf ? nullptr : static_cast<double*>(W), sm1, sm0, sn1, sn0, mdiv, ndiv, 1.0, beta};
-    if (bf) m.dst32 = static_cast<float*>(W);
-    return m;
-  };
-  // the twelve contractions: A, B, rows of A per pair, N, K, output map
-  struct Cfg {
-    const Packed* A;
-    const Packed* B;
-    int N, K;
-    OutMap C;
-  };
-  const Cfg cfg[kCfg] = {
-      {&X1, &Tv, o2, v, omap(ooo, oo, 1, o, o, o, 0.0)},    // G_i: (ai|bd) t_kj^cd
-      {&X1, &TvT, o2, v, omap(ooo, oo, 1, o, o, o, 1.0)},   // G_i: (ai|cd) t_jk^bd
-      {&T2x, &O1, o2, o, omap(ooo, oo, 1, o, o, o, 1.0)},   // G_i: -t_il^ab (ck|jl)
-      {&T2x, &O1T, o2, o, omap(ooo, oo, 1, o, o, o, 1.0)},  // G_i: -t_il^ac (bj|kl)
-      {&X2, &Tv, o2, v, omap(ooo, o, 1, oo, o, o, 1.0)},    // G_j: (bj|ad) t_ki^cd
-      {&T2y, &O1, o2, o, omap(ooo, o, 1, oo, o, o, 1.0)},   // G_j: -t_jl^ba (ck|il)
-      {&X2, &Tv, o2, v, omap(ooo, 1, o, oo, o, o, 1.0)},    // G_k: (ck|ad) t_ji^bd
-      {&T2y, &O1, o2, o, omap(ooo, 1, o, oo, o, o, 1.0)},   // G_k: -t_kl^ca (bj|il)
-      {&Tv, &X1, o, v, omap(oo, 1, 0, o, o, 1 << 30, 1.0)}, // G_4: t_ik^ad (bj|cd)
-      {&O1, &T2x, o, o, omap(oo, 1, 0, o, o, 1 << 30, 1.0)},// G_4: -(ai|kl) t_jl^bc
-      {&Tv, &X1, o, v, omap(oo, o, 0, 1, o, 1 << 30, 1.0)}, // G_6: t_ij^ad (ck|bd)
-      {&O1, &T2x, o, o, omap(oo, o, 0, 1, o, 1 << 30, 1.0)},// G_6: -(ai|jl) t_kl^cb
-  };
   const bool staged = 2LL * ooo * wsz + (3LL * oo + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
   const size_t esmem = 2 * ooo * wsz + (3 * oo + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
   if (staged) {
@@ -452,56 +428,83 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     else
       cudaFuncSetAttribute(k_t_energy_staged<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(esmem));
+  } else if (bf) {
+    cleanup();
+    set_error("lnocc_triples: nocc too large for the staged (T) energy kernel in this build");
+    return LNOCC_EINVAL;
   }
-  double* Wd = static_cast<double*>(W);
-  // per-pair row offsets of every contraction, uploaded once: entry [g][pair]
-  for (int p = 0; p < npair; ++p) {
-    const int b = hb[p], c = hc[p];
-    const int xb = b * v * o, xc = c * v * o;
-    const int Ma = (b + 1) * o, Ma2 = (b + 1) * o2;
-    const long long cb = static_cast<long long>(p % P) * slot_stride;
-    const int rows[kCfg][3] = {{xb, c * o2, Ma},     {xc, b * o2, Ma},     {xb, c * o2, Ma},     {xc, b * o2, Ma},
-                               {xb, c * o2, Ma},     {xb, c * o2, Ma},     {xc, b * o2, Ma},     {xc, b * o2, Ma},
-                               {0, xc + b * o, Ma2}, {0, xc + b * o, Ma2}, {0, xb + c * o, Ma2}, {0, xb + c * o, Ma2}};
-    for (int g = 0; g < kCfg; ++g)
-      hbat[static_cast<size_t>(g) * npair + p] = BatchEntry{rows[g][0], rows[g][1], rows[g][2], 0, cb};
-  }
-  cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
-  for (int p0 = 0; p0 < npair; p0 += P) {
-    const int np = std::min(P, npair - p0);
-    int maxb = 0;
-    for (int q = 0; q < np; ++q) maxb = std::max(maxb, hb[p0 + q]);
+  auto omap = [&](double beta) {
+    OutMap m{bf ? nullptr : static_cast<double*>(W), 0, 0, 0, 0, 1 << 30, 1 << 30, 1.0, beta};
+    if (bf) m.dst32 = static_cast<float*>(W);
+    return m;
+  };
+  const int o2 = static_cast<int>(oo);
+  for (const Chunk& ch : plan) {
+    const int b = ch.b, c0 = ch.c0, nc = ch.nc;
+    const int na = b + 1, Ma = na * o, Ma2 = na * o2;
+    const long long Sc = 1LL * na * ooo;  // W stride of c
+    const int xb = b * v * o;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    for (int g = 0; g < kCfg; ++g) {
-      const int maxM = (g < 8) ? (maxb + 1) * o : (maxb + 1) * o2;
-      gemm_batched(*cfg[g].A, *cfg[g].B, dbat + static_cast<size_t>(g) * npair + p0, np, maxM, cfg[g].N, cfg[g].K,
-                   cfg[g].C, s, dstatus);
+    // W layout [c - c0][a][i][k][j]; each term's d-part (K = v) and l-part (K = o) accumulate in TMEM.
+    // sigma1: rows (a,i), cols (c,k,j): (ai|bd) t_kj^cd - t_il^ab (ck|jl)   [first writer]
+    {
+      OutMap m = omap(0.0);
+      m.sm1 = ooo; m.sm0 = oo; m.mdiv = o;
+      m.sn2 = Sc; m.sn1 = o; m.sn0 = 1; m.ndiv = o; m.ndiv1 = o;
+      gemm2_off(X1, xb, Tv, c0 * o2, v, T2x, xb, O1, c0 * o2, o, Ma, nc * o2, m, s, dstatus);
+    }
+    // sigma3: rows (a,j), cols (c,k,i): (bj|ad) t_ki^cd - t_jl^ba (ck|il)
+    {
+      OutMap m = omap(1.0);
+      m.sm1 = ooo; m.sm0 = 1; m.mdiv = o;
+      m.sn2 = Sc; m.sn1 = o; m.sn0 = oo; m.ndiv = o; m.ndiv1 = o;
+      gemm2_off(X2, xb, Tv, c0 * o2, v, T2y, xb, O1, c0 * o2, o, Ma, nc * o2, m, s, dstatus);
+    }
+    // sigma4: rows (a,i,k), cols (c,j): t_ik^ad (bj|cd) - (ai|kl) t_jl^bc
+    {
+      OutMap m = omap(1.0);
+      m.sm2 = ooo; m.sm1 = oo; m.sm0 = o; m.mdiv = o; m.mdiv1 = o;
+      m.sn1 = Sc; m.sn0 = 1; m.ndiv = o;
+      gemm2_off(Tv, 0, X2, xb + c0 * o, v, O1, 0, T2y, xb + c0 * o, o, Ma2, nc * o, m, s, dstatus);
+    }
+    // sigma6: rows (a,i,j), cols (c,k): t_ij^ad (ck|bd) - (ai|jl) t_kl^cb
+    {
+      OutMap m = omap(1.0);
+      m.sm2 = ooo; m.sm1 = oo; m.sm0 = 1; m.mdiv = o; m.mdiv1 = o;
+      m.sn1 = Sc; m.sn0 = o; m.ndiv = o;
+      gemm2_off(Tv, 0, X1, xb + c0 * o, v, O1, 0, T2x, xb + c0 * o, o, Ma2, nc * o, m, s, dstatus);
+    }
+    // sigma2 (batched over c): rows (a,i), cols (k,j): (ai|cd) t_jk^bd - t_il^ac (bj|kl)
+    {
+      OutMap m = omap(1.0);
+      m.sm1 = ooo; m.sm0 = oo; m.mdiv = o;
+      m.sn1 = o; m.sn0 = 1; m.ndiv = o;
+      gemm2_batched(X1, TvT, &T2x, &O1T, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
+    }
+    // sigma5 (batched over c): rows (a,k), cols (j,i): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
+    {
+      OutMap m = omap(1.0);
+      m.sm1 = ooo; m.sm0 = o; m.mdiv = o;
+      m.sn1 = 1; m.sn0 = oo; m.ndiv = o;
+      gemm2_batched(X2, Tv, &T2y, &O1, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
     }
     cudaEventRecord(e1, s);
     gev.emplace_back(e0, e1);
-    if (staged) {
-      count_launch();
-      if (bf)
-        k_t_energy_staged<float, float><<<dim3(v, np), 256, esmem, s>>>(
-            static_cast<const float*>(W), slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
-      else
-        k_t_energy_staged<double, double><<<dim3(v, np), 256, esmem, s>>>(
-            Wd, slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
-    } else {
-      if (bf) {
-        set_error("lnocc_triples: nocc too large for the staged (T) energy kernel in this build");
-        cleanup();
-        return LNOCC_EINVAL;
-      }
-      count_launch();
-      k_t_energy<<<dim3(v, np), 128, 0, s>>>(Wd, slot_stride, dpb, dpc, p0, o, v, eps, t1, ovov, dU, nlo, tpart);
-    }
+    count_launch();
+    if (bf)
+      k_t_energy_staged<float, float><<<dim3(na, nc), 256, esmem, s>>>(
+          static_cast<const float*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo, tpart + 2 * ch.part);
+    else if (staged)
+      k_t_energy_staged<double, double><<<dim3(na, nc), 256, esmem, s>>>(
+          static_cast<const double*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo, tpart + 2 * ch.part);
+    else
+      k_t_energy<<<dim3(na, nc), 128, 0, s>>>(static_cast<const double*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo,
+                                              tpart + 2 * ch.part);
   }
-  count_launch();
-  k_t_finish<<<1, 1024, 0, s>>>(tpart, 1LL * npair * v, scal + 4);
+  k_t_finish<<<1, 1024, 0, s>>>(tpart, nblk_total, scal + 4);
   cudaMemcpyAsync(h_scal + 4, scal + 4, 16, cudaMemcpyDeviceToHost, s);
   cudaEventRecord(ev_call1, s);
   cudaStreamSynchronize(s);
