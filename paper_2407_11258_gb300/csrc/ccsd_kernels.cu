@@ -358,6 +358,30 @@ __global__ void k_dress_mats(const double* t1, double* X, double* Y, int o, int 
   }
 }
 
+// T1-transformed one-electron part h^ = (1 - T) h (1 + T), T[o+a][i] = t_i^a, written element by element:
+//   h^_pq = h_pq + [q occ] sum_c h_p,c t_q^c - [p vir] sum_k t_k^p h_kq - [p vir][q occ] sum_kc t_k^p h_kc t_q^c
+__global__ void k_hhat(const double* __restrict__ h, const double* __restrict__ t1, double* __restrict__ out, int o,
+                       int v) {
+  const int n = o + v;
+  GRID_STRIDE(idx, static_cast<long long>(n) * n) {
+    const int q = idx % n, p = idx / n;
+    double r = h[idx];
+    if (q < o)
+      for (int c = 0; c < v; ++c) r += h[p * n + o + c] * t1[q * v + c];
+    if (p >= o) {
+      const int a = p - o;
+      for (int k2 = 0; k2 < o; ++k2) {
+        const double tk = t1[k2 * v + a];
+        double s = h[k2 * n + q];
+        if (q < o)
+          for (int c = 0; c < v; ++c) s += h[k2 * n + o + c] * t1[q * v + c];
+        r -= tk * s;
+      }
+    }
+    out[idx] = r;
+  }
+}
+
 // xq[Q] = sum_k Boo[Q][k][k]
 __global__ void k_trace_oo(const double* Boo, int naux, int o, double* xq) {
   GRID_STRIDE(Q, naux) {
@@ -478,6 +502,10 @@ void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s) {
   count_launch();
   k_dress_mats<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(t1, X, Y, o, v);
+}
+void launch_hhat(const double* h, const double* t1, double* out, int o, int v, cudaStream_t s) {
+  count_launch();
+  k_hhat<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(h, t1, out, o, v);
 }
 void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s) {
   count_launch();

@@ -143,9 +143,13 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   const int c = c0 + slot;
   const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
   const int o2 = o * o, o3 = o2 * o;
+  // shared-memory blocks w and v use padded strides (S0 = o(o+1)+1, S1 = o+1, S2 = 1, all odd for
+  // even o) so that the permuted reads of the orderings below spread over the banks
+  const int S1 = o + 1, S0 = o * S1 + 1;
+  const int blk = o * S0;
   Real* sw = reinterpret_cast<Real*>(smraw);
-  Real* sv = sw + o3;
-  Real* Sab = sv + o3;      // (y0 a|y1 b)
+  Real* sv = sw + blk;
+  Real* Sab = sv + blk;     // (y0 a|y1 b)
   Real* Sac = Sab + o2;     // (y0 a|y2 c)
   Real* Sbc = Sac + o2;     // (y1 b|y2 c)
   Real* ta = Sbc + o2;      // t1[y][a], t1[y][b], t1[y][c]
@@ -170,9 +174,10 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   for (int idx = threadIdx.x; idx < o * nlo; idx += blockDim.x) Us[idx] = static_cast<Real>(U[idx]);
   __syncthreads();
   const TW* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
+  // W is stored [i][k][j] (j fastest): read it in that order (coalesced)
   for (int idx = threadIdx.x; idx < o3; idx += blockDim.x) {
-    const int y0 = idx / o2, y1 = (idx / o) % o, y2 = idx % o;
-    const Real Wv = static_cast<Real>(Wb[y0 * o2 + y2 * o + y1]);  // W stored [a][i][k][j]
+    const int y1 = idx % o, y2 = (idx / o) % o, y0 = idx / o2;
+    const Real Wv = static_cast<Real>(Wb[idx]);
     const Real disc = Sab[y0 * o + y1] * tc[y2] + Sac[y0 * o + y2] * tb[y1] + Sbc[y1 * o + y2] * ta[y0];
     const Real d = dm[y0] + dm[y1] + dm[y2];
     Real sc;
@@ -180,12 +185,13 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
       sc = static_cast<Real>(rsqrtf(static_cast<float>(d)));
     else
       sc = static_cast<Real>(1.0 / sqrt(static_cast<double>(d)));
-    sw[idx] = Wv * sc;
-    sv[idx] = (Wv + disc) * sc;
+    const int sidx = y0 * S0 + y1 * S1 + y2;
+    sw[sidx] = Wv * sc;
+    sv[sidx] = (Wv + disc) * sc;
   }
   __syncthreads();
   const int x[3] = {a, b, c};
-  const int S3[3] = {o2, o, 1};
+  const int S3[3] = {S0, S1, 1};
   double e_can = 0.0, e_frag = 0.0;
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
@@ -381,7 +387,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 
   // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
-  const long long welems = std::max<long long>((96LL << 20) / static_cast<long long>(wsz), v * ooo);
+  const long long welems = std::max<long long>((48LL << 20) / static_cast<long long>(wsz), v * ooo);
   void* W = tmp_alloc(static_cast<size_t>(welems) * wsz);
   long long nblk_total = 0;
   for (int b = 0; b < v; ++b) nblk_total += 1LL * (b + 1) * (v - b);
@@ -419,8 +425,9 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   }
   cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
 
-  const bool staged = 2LL * ooo * wsz + (3LL * oo + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
-  const size_t esmem = 2 * ooo * wsz + (3 * oo + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
+  const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
+  const bool staged = 2LL * sblk * wsz + (3LL * oo + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
+  const size_t esmem = 2 * sblk * wsz + (3 * oo + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
   if (staged) {
     if (bf)
       cudaFuncSetAttribute(k_t_energy_staged<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
