@@ -416,7 +416,7 @@ void Frag::iterate(bool fp64_residual) {
   const Consts& K = C();
   mark("dress");
   // ---- T1-transformed Fock matrix F^ = (1-T) h (1+T) + sum_Q [2 B^_Qpq x_Q - sum_k B^_Qpk B^_Qkq]
-  launch_hhat(h, t1, Fh, o, v, s);
+  launch_hhat(h, t1, tmpn, Fh, o, v, s);
   launch_trace_oo(Boo_h, N, o, xq, s);
   // Coulomb part, block by block (F^ laid out n x n: oo | ov / vo | vv)
   auto coul = [&](const double* Bblk, int rows, int cols, long long qstride, double* dst, long long ld) {

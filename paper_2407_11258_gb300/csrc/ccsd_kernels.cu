@@ -358,26 +358,30 @@ __global__ void k_dress_mats(const double* t1, double* X, double* Y, int o, int 
   }
 }
 
-// T1-transformed one-electron part h^ = (1 - T) h (1 + T), T[o+a][i] = t_i^a, written element by element:
-//   h^_pq = h_pq + [q occ] sum_c h_p,c t_q^c - [p vir] sum_k t_k^p h_kq - [p vir][q occ] sum_kc t_k^p h_kc t_q^c
-__global__ void k_hhat(const double* __restrict__ h, const double* __restrict__ t1, double* __restrict__ out, int o,
-                       int v) {
+// T1-transformed one-electron part h^ = (1 - T) h (1 + T), T[o+a][i] = t_i^a, in two steps:
+//   g_kq  = h_kq + [q occ] sum_c h_k,c t_q^c                    (occupied rows k of h (1 + T))
+//   h^_pq = h_pq + [q occ] sum_c h_p,c t_q^c - [p vir] sum_k t_k^p g_kq
+__global__ void k_hhat_rows(const double* __restrict__ h, const double* __restrict__ t1, double* __restrict__ g, int o,
+                            int v) {
+  const int n = o + v;
+  GRID_STRIDE(idx, static_cast<long long>(o) * n) {
+    const int q = idx % n, k2 = idx / n;
+    double r = h[k2 * n + q];
+    if (q < o)
+      for (int c = 0; c < v; ++c) r += h[k2 * n + o + c] * t1[q * v + c];
+    g[idx] = r;
+  }
+}
+__global__ void k_hhat(const double* __restrict__ h, const double* __restrict__ t1, const double* __restrict__ g,
+                       double* __restrict__ out, int o, int v) {
   const int n = o + v;
   GRID_STRIDE(idx, static_cast<long long>(n) * n) {
     const int q = idx % n, p = idx / n;
     double r = h[idx];
     if (q < o)
       for (int c = 0; c < v; ++c) r += h[p * n + o + c] * t1[q * v + c];
-    if (p >= o) {
-      const int a = p - o;
-      for (int k2 = 0; k2 < o; ++k2) {
-        const double tk = t1[k2 * v + a];
-        double s = h[k2 * n + q];
-        if (q < o)
-          for (int c = 0; c < v; ++c) s += h[k2 * n + o + c] * t1[q * v + c];
-        r -= tk * s;
-      }
-    }
+    if (p >= o)
+      for (int k2 = 0; k2 < o; ++k2) r -= t1[k2 * v + (p - o)] * g[k2 * n + q];
     out[idx] = r;
   }
 }
@@ -392,13 +396,27 @@ __global__ void k_trace_oo(const double* Boo, int naux, int o, double* xq) {
 }
 
 // dst[p*ld + q] += alpha * sum_Q B[Q*qstride + p*rstride + q] x[Q]
+// Block of 32 (p,q) x 8 Q-lanes: each lane sums every 8th Q, then a fixed-order reduction over the lanes.
 __global__ void k_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
                           int naux, double alpha, double* dst, long long ld) {
-  GRID_STRIDE(idx, static_cast<long long>(rows) * cols) {
-    const int q = idx % cols, p = idx / cols;
-    double acc = 0.0;
-    for (int Q = 0; Q < naux; ++Q) acc += B[Q * qstride + p * rstride + q] * x[Q];
-    dst[p * ld + q] += alpha * acc;
+  __shared__ double part[8][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const long long total = static_cast<long long>(rows) * cols;
+  const long long idx = static_cast<long long>(blockIdx.x) * 32 + tx;
+  double acc = 0.0;
+  if (idx < total) {
+    const int q = static_cast<int>(idx % cols), p = static_cast<int>(idx / cols);
+    const double* b = B + p * rstride + q;
+#pragma unroll 4
+    for (int Q = ty; Q < naux; Q += 8) acc += b[Q * qstride] * x[Q];
+  }
+  part[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && idx < total) {
+    double s = 0.0;
+    for (int l = 0; l < 8; ++l) s += part[l][tx];
+    const int q = static_cast<int>(idx % cols), p = static_cast<int>(idx / cols);
+    dst[p * ld + q] += alpha * s;
   }
 }
 
@@ -503,9 +521,10 @@ void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cud
   count_launch();
   k_dress_mats<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(t1, X, Y, o, v);
 }
-void launch_hhat(const double* h, const double* t1, double* out, int o, int v, cudaStream_t s) {
-  count_launch();
-  k_hhat<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(h, t1, out, o, v);
+void launch_hhat(const double* h, const double* t1, double* g, double* out, int o, int v, cudaStream_t s) {
+  count_launch(2);
+  k_hhat_rows<<<grid_for(1LL * o * (o + v)), kThreads, 0, s>>>(h, t1, g, o, v);
+  k_hhat<<<grid_for(1LL * (o + v) * (o + v)), kThreads, 0, s>>>(h, t1, g, out, o, v);
 }
 void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s) {
   count_launch();
@@ -514,7 +533,8 @@ void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_
 void launch_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
                     int naux, double alpha, double* dst, long long ld, cudaStream_t s) {
   count_launch();
-  k_coulomb<<<grid_for(1LL * rows * cols), kThreads, 0, s>>>(B, qstride, rows, cols, rstride, x, naux, alpha, dst, ld);
+  k_coulomb<<<static_cast<int>((1LL * rows * cols + 31) / 32), 256, 0, s>>>(B, qstride, rows, cols, rstride, x, naux,
+                                                                          alpha, dst, ld);
 }
 void launch_finite(const double* x, long long n, int* flag, cudaStream_t s) {
   count_launch();

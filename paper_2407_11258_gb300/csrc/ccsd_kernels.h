@@ -27,7 +27,7 @@ void launch_pair_dots(const double* tau, const double* L, int o, long long K, do
 void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s);
 void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s);
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s);
-void launch_hhat(const double* h, const double* t1, double* out, int o, int v, cudaStream_t s);
+void launch_hhat(const double* h, const double* t1, double* g, double* out, int o, int v, cudaStream_t s);
 void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s);
 void launch_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
                     int naux, double alpha, double* dst, long long ld, cudaStream_t s);

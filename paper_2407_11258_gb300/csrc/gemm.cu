@@ -199,11 +199,25 @@ __device__ __forceinline__ void store_at_f(const OutMap& C, long long off, float
   }
 }
 
-// Sixteen epilogue stores: all old values are loaded first (independent loads in flight together),
-// then combined and stored.
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// Sixteen epilogue stores. beta = 1 accumulates with fire-and-forget reductions (each element is
+// touched once per launch, so launches on one stream still add in a fixed order); other beta values
+// load all old values first (independent loads in flight together), then store.
 __device__ __forceinline__ void store16(const OutMap& C, const long long (&off)[16], const bool (&ok)[16],
                                         const float (&v)[16], float alpha, float beta) {
   if (C.dst32) {
+    if (beta == 1.f) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (ok[j]) red_add(C.dst32 + off[j], alpha * v[j]);
+      return;
+    }
     float old[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) old[j] = (beta != 0.f && ok[j]) ? C.dst32[off[j]] : 0.f;
@@ -211,6 +225,12 @@ __device__ __forceinline__ void store16(const OutMap& C, const long long (&off)[
     for (int j = 0; j < 16; ++j)
       if (ok[j]) C.dst32[off[j]] = fmaf(beta, old[j], alpha * v[j]);
   } else {
+    if (C.beta == 1.0) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (ok[j]) red_add(C.dst + off[j], static_cast<double>(alpha * v[j]));
+      return;
+    }
     double old[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) old[j] = (C.beta != 0.0 && ok[j]) ? C.dst[off[j]] : 0.0;
@@ -218,10 +238,7 @@ __device__ __forceinline__ void store16(const OutMap& C, const long long (&off)[
     for (int j = 0; j < 16; ++j)
       if (ok[j]) {
         double r = static_cast<double>(alpha * v[j]);
-        if (C.beta == 1.0)
-          r += old[j];
-        else if (C.beta != 0.0)
-          r += C.beta * old[j];
+        if (C.beta != 0.0) r += C.beta * old[j];
         C.dst[off[j]] = r;
       }
   }

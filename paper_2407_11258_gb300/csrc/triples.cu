@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "ccsd_kernels.h"
@@ -149,10 +150,11 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   const int blk = o * S0;
   Real* sw = reinterpret_cast<Real*>(smraw);
   Real* sv = sw + blk;
+  const int P1 = o + 1, o2p = o * P1;  // o x o slices padded to odd row stride
   Real* Sab = sv + blk;     // (y0 a|y1 b)
-  Real* Sac = Sab + o2;     // (y0 a|y2 c)
-  Real* Sbc = Sac + o2;     // (y1 b|y2 c)
-  Real* ta = Sbc + o2;      // t1[y][a], t1[y][b], t1[y][c]
+  Real* Sac = Sab + o2p;    // (y0 a|y2 c)
+  Real* Sbc = Sac + o2p;    // (y1 b|y2 c)
+  Real* ta = Sbc + o2p;     // t1[y][a], t1[y][b], t1[y][c]
   Real* tb = ta + o;
   Real* tc = tb + o;
   Real* dm = tc + o;        // d_m
@@ -161,9 +163,9 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
   for (int idx = threadIdx.x; idx < o2; idx += blockDim.x) {
     const int p = idx / o, q = idx % o;
-    Sab[idx] = static_cast<Real>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + b]);
-    Sac[idx] = static_cast<Real>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + c]);
-    Sbc[idx] = static_cast<Real>(ovov[(1LL * p * v + b) * ov + 1LL * q * v + c]);
+    Sab[p * P1 + q] = static_cast<Real>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + b]);
+    Sac[p * P1 + q] = static_cast<Real>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + c]);
+    Sbc[p * P1 + q] = static_cast<Real>(ovov[(1LL * p * v + b) * ov + 1LL * q * v + c]);
   }
   for (int y = threadIdx.x; y < o; y += blockDim.x) {
     ta[y] = static_cast<Real>(t1[y * v + a]);
@@ -178,7 +180,7 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   for (int idx = threadIdx.x; idx < o3; idx += blockDim.x) {
     const int y1 = idx % o, y2 = (idx / o) % o, y0 = idx / o2;
     const Real Wv = static_cast<Real>(Wb[idx]);
-    const Real disc = Sab[y0 * o + y1] * tc[y2] + Sac[y0 * o + y2] * tb[y1] + Sbc[y1 * o + y2] * ta[y0];
+    const Real disc = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
     const Real d = dm[y0] + dm[y1] + dm[y2];
     Real sc;
     if (sizeof(Real) == 4)
@@ -190,38 +192,49 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
     sv[sidx] = (Wv + disc) * sc;
   }
   __syncthreads();
-  const int x[3] = {a, b, c};
-  const int S3[3] = {S0, S1, 1};
-  double e_can = 0.0, e_frag = 0.0;
+  // the six slot permutations; with the loop fully unrolled every index below is a compile-time choice
+  constexpr int PM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int x0 = a, x1 = b, x2 = c;
+  Real r_can = 0, r_frag = 0;  // per-thread partials (converted to FP64 for the block sum)
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
+#pragma unroll
     for (int pi = 0; pi < 6; ++pi) {
-      const int p0 = kPerm[pi][0], p1 = kPerm[pi][1], p2 = kPerm[pi][2];
+      const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
+      auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
+      auto SS = [&](int p) { return p == 0 ? S0 : (p == 1 ? S1 : 1); };
       bool dup = false;
-      for (int q = 0; q < pi && !dup; ++q)
-        dup = x[kPerm[q][0]] == x[p0] && x[kPerm[q][1]] == x[p1] && x[kPerm[q][2]] == x[p2];
+#pragma unroll
+      for (int q = 0; q < pi; ++q)
+        dup = dup || (X(PM[q][0]) == X(p0) && X(PM[q][1]) == X(p1) && X(PM[q][2]) == X(p2));
       if (dup) continue;
       // offsets of W^{abc}_y for the four orderings: T (p0,p1,p2), T o c (p1,p2,p0), T o c^2 (p2,p0,p1),
       // reversed (p2,p1,p0); slot p receives i, j or k.
-      const int base0 = j * S3[p1] + k * S3[p2], si0 = S3[p0];
-      const int base1 = j * S3[p2] + k * S3[p0], si1 = S3[p1];
-      const int base2 = j * S3[p0] + k * S3[p1], si2 = S3[p2];
-      const int base3 = j * S3[p1] + k * S3[p0], si3 = S3[p2];
+      const int base0 = j * SS(p1) + k * SS(p2), si0 = SS(p0);
+      const int base1 = j * SS(p2) + k * SS(p0), si1 = SS(p1);
+      const int base2 = j * SS(p0) + k * SS(p1), si2 = SS(p2);
+      const int base3 = j * SS(p1) + k * SS(p0), si3 = SS(p2);
       Real acc = 0, zu[8], yu[8];
+#pragma unroll
       for (int al = 0; al < 8; ++al) zu[al] = yu[al] = 0;
       for (int i = 0; i < o; ++i) {
         const Real z = 4 * sw[base0 + i * si0] + sw[base1 + i * si1] + sw[base2 + i * si2];
         const Real y = sv[base0 + i * si0] - sv[base3 + i * si3];
         acc += z * y;
-        for (int al = 0; al < nlo; ++al) {
-          zu[al] += Us[i * nlo + al] * z;
-          yu[al] += Us[i * nlo + al] * y;
-        }
+#pragma unroll
+        for (int al = 0; al < 8; ++al)
+          if (al < nlo) {
+            zu[al] += Us[i * nlo + al] * z;
+            yu[al] += Us[i * nlo + al] * y;
+          }
       }
-      e_can += static_cast<double>(acc);
-      for (int al = 0; al < nlo; ++al) e_frag += static_cast<double>(zu[al]) * static_cast<double>(yu[al]);
+      r_can += acc;
+#pragma unroll
+      for (int al = 0; al < 8; ++al)
+        if (al < nlo) r_frag += zu[al] * yu[al];
     }
   }
+  double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
   __shared__ double sh[2][32];
   for (int off = 16; off > 0; off >>= 1) {
     e_can += __shfl_xor_sync(0xffffffffu, e_can, off);
@@ -387,7 +400,9 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 
   // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
-  const long long welems = std::max<long long>((48LL << 20) / static_cast<long long>(wsz), v * ooo);
+  long long chunk_mb = 48;
+  if (const char* e = std::getenv("LNOCC_TCHUNK_MB")) chunk_mb = std::max(1, std::atoi(e));
+  const long long welems = std::max<long long>((chunk_mb << 20) / static_cast<long long>(wsz), v * ooo);
   void* W = tmp_alloc(static_cast<size_t>(welems) * wsz);
   long long nblk_total = 0;
   for (int b = 0; b < v; ++b) nblk_total += 1LL * (b + 1) * (v - b);
@@ -426,8 +441,9 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
 
   const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
-  const bool staged = 2LL * sblk * wsz + (3LL * oo + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
-  const size_t esmem = 2 * sblk * wsz + (3 * oo + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
+  const bool staged = 2LL * sblk * wsz + (3LL * o * (o + 1) + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
+  const size_t esmem =
+      2 * sblk * wsz + (3 * static_cast<size_t>(o) * (o + 1) + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
   if (staged) {
     if (bf)
       cudaFuncSetAttribute(k_t_energy_staged<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
