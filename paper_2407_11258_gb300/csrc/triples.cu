@@ -400,7 +400,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 
   // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
-  long long chunk_mb = 48;
+  long long chunk_mb = 192;
   if (const char* e = std::getenv("LNOCC_TCHUNK_MB")) chunk_mb = std::max(1, std::atoi(e));
   const long long welems = std::max<long long>((chunk_mb << 20) / static_cast<long long>(wsz), v * ooo);
   void* W = tmp_alloc(static_cast<size_t>(welems) * wsz);
