@@ -145,6 +145,22 @@ int lnocc_triples(lnocc_frag* f, int nlo, const double* U_frag, double* e_t_full
  */
 int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const double* B, double* C, void* stream);
 
+/*
+ * lnocc_gemm_noalloc -- C[M][N] = A[M][K] B[N][K]^T like lnocc_debug_gemm, but without allocating device
+ * memory. The paper has no counterpart: this serves callers that cannot call cudaMalloc -- code running
+ * under a fixed device-memory budget owned by another allocator, or code that must not synchronize the
+ * device, which cudaMalloc / cudaFree can do.
+ *   Working memory is a file-scope __device__ array of 32 MiB that every GPU loading the library holds until
+ *   the process exits; the packed operands need (M + N) * roundup(K, 64) * (8 bytes FP64 | 4 bytes mixed)
+ *   plus 256 bytes, and larger requests return LNOCC_EINVAL before any device work.
+ *   The first call on a device looks up that array's device address (cudaGetSymbolAddress, with the device
+ *   current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents: calls that overlap on the GPU (other
+ *   streams, other host threads) race on it. The call synchronizes `stream` before it returns.
+ *   Device pointers, row-major FP64; precision LNOCC_PREC_FP64 or LNOCC_PREC_MIXED.
+ */
+int lnocc_gemm_noalloc(int precision, int M, int N, int K, const double* A, const double* B, double* C, void* stream);
+
 /* Copy the handle's bookkeeping (energies, iteration count, flop counters) into *info. */
 int lnocc_frag_info(const lnocc_frag* f, lnocc_info* info);
 

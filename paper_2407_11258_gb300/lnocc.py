@@ -21,7 +21,8 @@ ERR_NAMES = {0: "LNOCC_OK", 1: "LNOCC_EINVAL", 2: "LNOCC_ENOMEM", 3: "LNOCC_ENOC
              5: "LNOCC_ETIMEOUT", 6: "LNOCC_ECUDA"}
 
 EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragment_energy", "lnocc_triples",
-           "lnocc_debug_gemm", "lnocc_frag_info", "lnocc_free_fragment", "lnocc_last_error", "lnocc_version"]
+           "lnocc_debug_gemm", "lnocc_gemm_noalloc", "lnocc_frag_info", "lnocc_free_fragment", "lnocc_last_error",
+           "lnocc_version"]
 
 
 class Opts(ctypes.Structure):
@@ -65,12 +66,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lnocc_fragment_energy.argtypes = [P, I, P, ctypes.POINTER(D), ctypes.POINTER(D), P]
     lib.lnocc_triples.argtypes = [P, I, P, ctypes.POINTER(D), ctypes.POINTER(D), P]
     lib.lnocc_debug_gemm.argtypes = [I, I, I, I, P, P, P, P]
+    lib.lnocc_gemm_noalloc.argtypes = [I, I, I, I, P, P, P, P]
     lib.lnocc_frag_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lnocc_free_fragment.argtypes = [P]
     lib.lnocc_last_error.restype = ctypes.c_char_p
     lib.lnocc_version.restype = ctypes.c_char_p
     for name in ("lnocc_build_ints", "lnocc_ccsd", "lnocc_fragment_energy", "lnocc_triples", "lnocc_debug_gemm",
-                 "lnocc_frag_info", "lnocc_free_fragment"):
+                 "lnocc_gemm_noalloc", "lnocc_frag_info", "lnocc_free_fragment"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -168,4 +170,12 @@ def lnocc_debug_gemm(precision, A, B, C, stream=None):
     M, K = A.shape
     N = B.shape[0]
     _check(load().lnocc_debug_gemm(precision, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
+    return C
+
+
+def lnocc_gemm_noalloc(precision, A, B, C, stream=None):
+    """C = A @ B.T through the contraction engine using the library's fixed scratch (no device allocation)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load().lnocc_gemm_noalloc(precision, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
     return C
