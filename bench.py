@@ -6,11 +6,18 @@ A step is one pass of the whole per-fragment hot path through the C-ABI: integra
 in for the paper's diamond fragment (seeded generator in paper_2407_11258_gb300/synth.py).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-fp64] [--no-cpu]
+    python bench.py --workload batch [--nfrag 128] [--workers 0] [--autotune 1] [--steps 1] [--warmup 1]
+    python bench.py --workload mlp [--ntrain 256] [--nheld 64] [--train-steps 2000] [--mlp-precision mixed]
 
 Prints one JSON line (rank 0). `value` is model TFLOP/s of whole solves with inputs resident in HBM
 (inputs of 0.5 GB exceed the 129 MB L2, so no flush is needed between steps); `e2e` repeats the
 measurement with the inputs in pinned host memory, copied in every step, and the energies read back.
 Multi-GPU runs shard independent fragments (one per rank per step) with no collective in the data path.
+
+`--workload batch` instead times whole batches of uneven fragments (nocc U{8..24}, nvir U{120..360},
+naux = 4 nvir, half small-gap) through lnocc_solve_batch: a step is one batch, `value` its model
+TFLOP/s and `solves_per_s` fragments per second. `--workload mlp` trains the learned T2 guess on GPU
+solves and reports held-out CCSD iteration counts and times from the MP2 and the learned guess.
 """
 from __future__ import annotations
 
@@ -214,6 +221,145 @@ def solve_once(lnocc, fr_dev, opts, stream):
                 t_gemm_ms=info.t_triples_gemm_ms, t_triples_ms=info.t_triples_ms, launches=info.kernel_launches)
 
 
+def run_batch(args):
+    """Uneven-fragment batch through lnocc_solve_batch; one step = the whole batch."""
+    import torch
+    from paper_2407_11258_gb300 import build, lnocc, synth
+    world, rank, local = dist_setup()
+    build.build()
+    lnocc.load()
+    stream = torch.cuda.Stream()
+    seed = 3000 + 100000 * rank  # weak scaling: every rank solves its own batch
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        items = [synth.batch_fragment_device(f, "cuda", nfrag=args.nfrag, seed=seed) for f in range(args.nfrag)]
+    stream.synchronize()
+    t_gen = time.perf_counter() - t0
+    opts = lnocc.default_opts(precision=lnocc.LNOCC_PREC_MIXED, max_iter=200)
+    mk = lambda tune: lnocc.default_batch_opts(workers=args.workers, autotune=tune)  # noqa: E731
+    # the first warm-up batch tunes the tiles (autotune 1); later batches reuse the table (autotune 2)
+    for w in range(args.warmup):
+        tune = (1 if w == 0 else 2) if args.autotune else 0
+        st, res = lnocc.lnocc_solve_batch(items, opts, mk(tune), stream=stream, allow_noconv=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    times = []
+    with sampler:
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            st, res = lnocc.lnocc_solve_batch(items, opts, mk(2 if args.autotune else 0), stream=stream,
+                                              allow_noconv=True)
+            times.append(time.perf_counter() - t1)
+    barrier(world)
+    sec = max_over_ranks(world, float(np.mean(times)))
+    flops = sum(r.model_flops for r in res)
+    if rank != 0:
+        return
+    peak_burst, peak_sust, hbm, peak_src = read_peaks()
+    achieved = world * flops / sec / 1e12
+    n_ok = sum(r.status == lnocc.LNOCC_OK for r in res)
+    busy = sum(r.t_end_ms - r.t_start_ms for r in res) / 1e3
+    print(json.dumps({
+        "metric": METRIC, "value": achieved, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/fp32 (fp64 update, DIIS, energies)", "data": "synthetic",
+        "config": {"workload": f"uneven batch of {args.nfrag} fragments: nocc U{{8..24}}, nvir U{{120..360}}, "
+                               f"naux=4*nvir, half small-gap (seed {seed})",
+                   "l2": "inputs (88 GB for 128 fragments) far larger than L2; no flush",
+                   "workers": args.workers, "autotune": args.autotune},
+        "solves_per_s": world * args.nfrag / sec, "converged": n_ok, "n_frag": args.nfrag,
+        "mean_ccsd_iterations": float(np.mean([r.n_iter for r in res])),
+        "pipeline_occupancy": busy / sec,
+        "input_generation_s": t_gen,
+        "e2e": None, "e2e_note": "not measured for the batch workload (88 GB of inputs)",
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_burst / 3.0, "unit": "TFLOP/s",
+                     "frac": achieved / (peak_burst / 3.0), "traffic": None,
+                     "kernel": "whole batch (model flops / wall time)",
+                     "note": f"peak = {peak_src} bf16 burst {peak_burst} / 3 (BF16x3)"},
+        "autotune_stats": lnocc.lnocc_autotune_stats(),
+        "clocks": sampler.summary(),
+    }), flush=True)
+
+
+def run_mlp(args):
+    """Learned T2 guess: generate training solves on the GPU, train the MLP with the library's kernels,
+    then solve held-out fragments from the MP2 guess and from the learned guess."""
+    import torch
+    from paper_2407_11258_gb300 import build, lnocc, synth
+    world, rank, local = dist_setup()
+    build.build()
+    lnocc.load()
+    dev = "cuda"
+    stream = torch.cuda.current_stream()
+    prec = lnocc.LNOCC_PREC_MIXED if args.mlp_precision == "mixed" else lnocc.LNOCC_PREC_FP64
+    per_frag = 4096
+    t0 = time.perf_counter()
+    Xs, dts, it_train = [], [], []
+    for k in range(args.ntrain):
+        o, v, q, eps, B, U = synth.mlp_fragment_device(k, dev)
+        f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=prec))
+        _, it, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
+        it_train.append(it)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(100 + k)
+        idx = torch.randint(0, o * o * v * v, (per_frag,), generator=gen, device=dev, dtype=torch.int64)
+        X = torch.empty(per_frag, 8, dtype=torch.float32, device=dev)
+        dt = torch.empty(per_frag, dtype=torch.float32, device=dev)
+        lnocc.lnocc_mlp_samples(f, idx, X, dt)
+        Xs.append(X)
+        dts.append(dt)
+        f.free()
+        del B
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    X, dt = torch.cat(Xs), torch.cat(dts)
+    m = lnocc.Mlp(synth.mlp_init(5100))
+    m.fit_norm(X, dt)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    t0 = time.perf_counter()
+    losses = []
+    for step in range(args.train_steps):
+        sel = torch.randint(0, X.shape[0], (args.batch,), generator=gen, device=dev)
+        lr = 3e-3 if step < 0.7 * args.train_steps else 1e-3
+        losses.append(m.train_step(X[sel].contiguous(), dt[sel].contiguous(), lr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    it0, it1, t_mp2, t_mlp, de, fallbacks = [], [], [], [], [], 0
+    for k in range(2000, 2000 + args.nheld):
+        o, v, q, eps, B, U = synth.mlp_fragment_device(k, dev)
+        f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=prec))
+        lnocc.lnocc_frag_set_mlp(f, m)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        e0, n0, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
+        b = time.perf_counter()
+        e1, n1, _ = lnocc.lnocc_ccsd(f, guess_mode=lnocc.LNOCC_GUESS_MLP, allow_noconv=True)
+        c = time.perf_counter()
+        it0.append(n0)
+        it1.append(n1)
+        t_mp2.append(b - a)
+        t_mlp.append(c - b)
+        de.append(abs(e1 - e0))
+        f.free()
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": args.nheld / sum(t_mlp), "unit": "CCSD solves/s (held-out, learned guess)",
+        "n_gpus": world, "steps": args.nheld, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/fp32" if prec else "f64", "data": "synthetic",
+        "config": {"workload": f"learned T2 guess: {args.ntrain} training solves, {args.nheld} held-out fragments, "
+                               f"nocc U{{8..16}}, nvir U{{96..240}}, naux=4*nvir, half small-gap",
+                   "samples_per_fragment": per_frag, "train_steps": args.train_steps, "batch": args.batch},
+        "mean_iterations_mp2_guess": float(np.mean(it0)), "mean_iterations_mlp_guess": float(np.mean(it1)),
+        "mean_ccsd_s_mp2_guess": float(np.mean(t_mp2)), "mean_ccsd_s_mlp_guess": float(np.mean(t_mlp)),
+        "max_abs_dE_mlp_vs_mp2_guess": float(np.max(de)),
+        "train_loss_first": float(np.mean(losses[:10])), "train_loss_last": float(np.mean(losses[-50:])),
+        "t_training_data_s": t_data, "t_training_s": t_train, "mean_iterations_training_solves": float(np.mean(it_train)),
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,9 +368,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="diamond", choices=["diamond", "batch", "mlp"])
+    ap.add_argument("--ntrain", type=int, default=256, help="mlp workload: training solves")
+    ap.add_argument("--nheld", type=int, default=64, help="mlp workload: held-out fragments")
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--mlp-precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nfrag", type=int, default=128, help="batch workload: fragments per batch")
+    ap.add_argument("--workers", type=int, default=0, help="batch workload: concurrent pipelines (0: library default)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1], help="batch workload: tile autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
 
     import torch
     from paper_2407_11258_gb300 import build, lnocc, synth

@@ -44,6 +44,7 @@ extern "C" {
 
 #define LNOCC_GUESS_MP2 0   /* t1 = 0, t2 = first-order amplitudes (Eq. 11, canonical form) */
 #define LNOCC_GUESS_GIVEN 1 /* start from t1_in / t2_in (restart / checkpoint resume) */
+#define LNOCC_GUESS_MLP 2   /* t1 = 0, t2 = learned guess of the model attached by lnocc_frag_set_mlp */
 
 #define LNOCC_FAULT_NAN_INPUT 1 /* fault injection (host side): poison one element of the B copy */
 #define LNOCC_FAULT_ZERO_DIIS 2 /* fault injection: run without DIIS extrapolation */
@@ -59,7 +60,9 @@ typedef struct lnocc_opts {
   double conv_energy; /* convergence: |E_k - E_k-1| below this (default 1e-10 Eh) */
   int fault_inject;   /* LNOCC_FAULT_* bitmask, 0 in production */
   int verbose;        /* 1: print one line per iteration to stderr */
-  int reserved[6];
+  int graph;          /* 1 (default): after the first iteration, replay each CCSD iteration from a CUDA
+                         graph captured once per fragment (same kernels, same results; fewer host launches) */
+  int reserved[5];
 } lnocc_opts;
 
 typedef struct lnocc_info {
@@ -110,6 +113,9 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
  * The converged amplitudes stay in the handle for lnocc_triples / lnocc_fragment_energy. The same
  * convergence test applies to every guess mode. Returns LNOCC_ENOCONV (with the last energy) when
  * max_iter is reached, LNOCC_ENUMERIC on NaN/Inf.
+ * LNOCC_GUESS_MLP falls back to the MP2 guess when the learned guess has a non-finite element, and
+ * repeats the solve from the MP2 guess when the run from the learned guess ends in ENOCONV or
+ * ENUMERIC (n_iter then counts both runs).
  */
 int lnocc_ccsd(lnocc_frag* f, const double* t1_in, const double* t2_in, int guess_mode, double* t1_out,
                double* t2_out, double* e_corr, int* n_iter, void* stream);
@@ -160,6 +166,131 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
  *   Device pointers, row-major FP64; precision LNOCC_PREC_FP64 or LNOCC_PREC_MIXED.
  */
 int lnocc_gemm_noalloc(int precision, int M, int N, int K, const double* A, const double* B, double* C, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * Batched fragments.
+ *
+ * The total correlation energy is a sum of fragment contributions (Eq. ecorr_cc, Sec. 2.2) and each
+ * fragment's local CCSD(T) uses only that fragment's active-space integrals, so the fragments of a
+ * calculation are independent problems. lnocc_solve_batch runs many of them -- of uneven
+ * (nocc, nvir, naux) -- on one GPU: longest-processing-time-first order on a flop cost model,
+ * `workers` concurrent pipelines (one host thread and one stream each) admitted under a device-memory
+ * budget, one stream-ordered memory pool for all fragment buffers, and each fragment's CCSD iterations
+ * replayed from a captured CUDA graph (opts->graph). Every fragment goes through exactly the same
+ * build / CCSD / fragment-energy / (T) code as the single-fragment calls with the same opts, so its
+ * energies equal those of lnocc_build_ints + lnocc_ccsd + lnocc_fragment_energy + lnocc_triples.
+ * ---------------------------------------------------------------------------------------------- */
+#define LNOCC_ORDER_LPT 0   /* longest processing time first (default) */
+#define LNOCC_ORDER_INPUT 1 /* the order of items[] */
+
+typedef struct lnocc_batch_item {
+  int nocc, nvir, naux; /* sizes of this fragment's active space */
+  int nlo;              /* columns of U_frag (0: canonical energies only, no projection) */
+  const double* eps;    /* device [nocc+nvir], occupied then virtual, every virtual above every occupied */
+  const double* B;      /* device [naux][n][n], symmetric in (p, q) */
+  const double* U_frag; /* device [nocc][nlo] fragment LO coefficients, or NULL when nlo == 0 */
+} lnocc_batch_item;
+
+typedef struct lnocc_batch_opts {
+  int workers;          /* concurrent fragment pipelines, 1..16 (0: 3) */
+  int triples;          /* 1 (default): (T) after CCSD */
+  int order;            /* LNOCC_ORDER_* */
+  int autotune;         /* 0: tiles as the library's autotune mode says (lnocc_autotune); 1: first time the
+                           GEMM tile candidates on up to 5 representative fragments (cost quantiles), then
+                           use the table for the batch; 2: use the loaded table only */
+  double mem_budget_gb; /* device memory the batch may hold at once, 1e9 bytes (0: 90% of free memory) */
+  int reserved[8];
+} lnocc_batch_opts;
+
+typedef struct lnocc_batch_result {
+  int status;           /* LNOCC_* of this fragment; ENOCONV keeps the last energies */
+  int n_iter;           /* CCSD iterations */
+  int worker;           /* pipeline that solved it */
+  int order;            /* position in which it was started */
+  double e_mp2, e_ccsd, e_mp2_frag, e_ccsd_frag, e_t, e_t_frag; /* Eh; *_frag are 0 when nlo == 0 */
+  double t_start_ms, t_end_ms; /* host wall clock since the start of the batch */
+  double model_flops;   /* (2o^2v^4 + 16o^3v^3 + 2o^4v^2) n_iter + (6o^3v^4 + 6o^4v^3) when (T) ran */
+  long long device_bytes; /* device memory held by the fragment handle */
+  double cost_estimate;   /* the scheduler's cost model (flops): LPT starts fragments in decreasing order */
+  long long bytes_estimate; /* the scheduler's device-memory estimate used for admission */
+} lnocc_batch_result;
+
+/* Defaults: workers 0 (auto), triples 1, LPT order, autotune 0, memory budget 0 (auto). */
+void lnocc_default_batch_opts(lnocc_batch_opts* b);
+
+/*
+ * lnocc_solve_batch -- solve nfrag independent fragments; returns when all are done.
+ *   items   : host array of nfrag descriptions (device pointers inside; they must stay valid and
+ *             unchanged until the call returns; work on `stream` that produces them is waited for).
+ *   opts    : per-fragment options as for lnocc_build_ints (NULL: defaults).
+ *   bopts   : scheduling options (NULL: defaults).
+ *   results : host array of nfrag results, written by the call.
+ *   Returns LNOCC_OK when every fragment converged, LNOCC_ENOCONV when some did not (their results
+ *   say so), else the status of a failing fragment (lnocc_last_error names it). The call allocates
+ *   its own device memory (a pool released on return) and host threads.
+ */
+int lnocc_solve_batch(int nfrag, const lnocc_batch_item* items, const lnocc_opts* opts, const lnocc_batch_opts* bopts,
+                      lnocc_batch_result* results, void* stream);
+
+/*
+ * Tile autotuner of the tensor-core GEMM (library-wide, all fragments; no counterpart in the paper).
+ * The CTA tile width BN (32..256) of every tcgen05 contraction is picked per shape bucket
+ * (M and K blocks in half-octaves, N in steps of 16, one or two K segments).
+ *   mode 0 (default): fixed rule (narrowest BN covering N);
+ *   mode 1: table lookup, fixed rule on a miss;
+ *   mode 2: like 1, but a miss first times every candidate on the call's own operands (into scratch,
+ *           synchronously on the call's stream) and stores the winner. Use from one thread at a time.
+ * lnocc_autotune sets the mode (mode < 0: only read it) and returns the previous one in *prev_mode.
+ * The table persists as a text file (lnocc_autotune_save / _load; load merges).
+ */
+int lnocc_autotune(int mode, int* prev_mode);
+int lnocc_autotune_save(const char* path);
+int lnocc_autotune_load(const char* path);
+/* entries in the table, lookups that hit / missed, shapes timed so far */
+int lnocc_autotune_stats(long long* entries, long long* hits, long long* misses, long long* tuned);
+
+/* ------------------------------------------------------------------------------------------------
+ * Learned T2 initial guess (no counterpart in the paper, whose CCSD starts from the MP2 amplitudes of
+ * Eq. 11): t_ij^ab = t_ij^ab(MP2) + s_out g(x_ijab), g an MLP 8 -> 128 -> 128 -> 1 with SiLU on the
+ * standardised features x = [t_MP2, e_i, e_j, e_a, e_b, D_ij^ab, (ia|jb), (ib|ja)] of the canonical
+ * member of {(i,j,a,b), (j,i,b,a)} (i < j, or i == j and a <= b). Training: mean squared error of g
+ * against (t_converged - t_MP2) / s_out, Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Parameter vector (float, lnocc_mlp_nparams() = 17793 values): W1[128][8], b1[128], W2[128][128],
+ * b2[128], w3[128], b3[1], row-major with the output index first. Standardisation ("norm", 17 doubles):
+ * feature means [8], standard deviations [8], s_out.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct lnocc_mlp lnocc_mlp; /* opaque: parameters, Adam state and workspace on the device */
+
+int lnocc_mlp_nparams(void);
+/* New model from host parameters (float[nparams]); norm starts as mean 0, deviation 1, s_out 1. */
+int lnocc_mlp_create(const float* params, lnocc_mlp** out);
+int lnocc_mlp_free(lnocc_mlp* m);
+/* Copy parameters (host float[nparams]) and / or norm (host double[17]) out; either may be NULL. */
+int lnocc_mlp_get(const lnocc_mlp* m, float* params, double* norm);
+/* Set the standardisation (host double[17]; deviations and s_out must be positive). */
+int lnocc_mlp_set_norm(lnocc_mlp* m, const double* norm);
+/*
+ * Training samples of a solved fragment: for n flat amplitude indices idx (device int64,
+ * ((i*o + j)*v + a)*v + b), the raw features X (device float[n][8]) and, when dt != NULL, the targets
+ * dt = t_converged - t_MP2 (device float[n]; needs a previous lnocc_ccsd on f).
+ */
+int lnocc_mlp_samples(const lnocc_frag* f, int n, const long long* idx, float* X, float* dt, void* stream);
+/* Standardisation from samples: feature means / deviations and s_out = rms(dt) (device reductions). */
+int lnocc_mlp_fit_norm(lnocc_mlp* m, int n, const float* X, const float* dt, void* stream);
+/* One Adam step on the minibatch (X, dt): forward, backward and update on the device (FP32); the
+ * batch loss before the step goes to *loss (host, may be NULL). */
+int lnocc_mlp_train_step(lnocc_mlp* m, int n, const float* X, const float* dt, float lr, double* loss, void* stream);
+/* Network output y[n] (device double) for raw features X; precision LNOCC_PREC_FP64 runs the FP64
+ * build of the training kernels, LNOCC_PREC_MIXED the FP32 one (checks). */
+int lnocc_mlp_forward(const lnocc_mlp* m, int precision, int n, const float* X, double* y, void* stream);
+/* Loss gradient (device double[nparams]) and loss (host) on (X, dt) without updating (checks). */
+int lnocc_mlp_grad(const lnocc_mlp* m, int precision, int n, const float* X, const float* dt, double* grad,
+                   double* loss, void* stream);
+/* The learned guess of a built fragment into t2_out (device double[o][o][v][v]); layer 2 runs as a
+ * BF16 tcgen05 MMA with FP32 accumulation. */
+int lnocc_mlp_guess(lnocc_frag* f, const lnocc_mlp* m, double* t2_out, void* stream);
+/* Attach (or detach with NULL) the model used by LNOCC_GUESS_MLP; the model must outlive its use. */
+int lnocc_frag_set_mlp(lnocc_frag* f, const lnocc_mlp* m);
 
 /* Copy the handle's bookkeeping (energies, iteration count, flop counters) into *info. */
 int lnocc_frag_info(const lnocc_frag* f, lnocc_info* info);

@@ -29,6 +29,7 @@ void lnocc_default_opts(lnocc_opts* o) {
   o->conv_energy = 1e-10;
   o->fault_inject = 0;
   o->verbose = 0;
+  o->graph = 1;
 }
 
 const char* lnocc_last_error(void) { return lnocc::g_last_error.c_str(); }
@@ -47,7 +48,7 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
   lnocc_default_opts(&o);
   if (opts) o = *opts;
   if ((o.precision != LNOCC_PREC_FP64 && o.precision != LNOCC_PREC_MIXED) || o.max_iter < 0 || o.diis_space < 0 ||
-      o.diis_space > 8 || o.n_refine < 0 || !(o.conv_rms > 0) || !(o.conv_energy > 0)) {
+      o.diis_space > 8 || o.n_refine < 0 || (o.graph != 0 && o.graph != 1) || !(o.conv_rms > 0) || !(o.conv_energy > 0)) {
     lnocc::set_error("lnocc_build_ints: bad options");
     return LNOCC_EINVAL;
   }
@@ -76,14 +77,14 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
 int lnocc_ccsd(lnocc_frag* h, const double* t1_in, const double* t2_in, int guess_mode, double* t1_out,
                double* t2_out, double* e_corr, int* n_iter, void* stream) {
   lnocc::set_error("");
-  if (!h || (guess_mode != LNOCC_GUESS_MP2 && guess_mode != LNOCC_GUESS_GIVEN)) {
+  if (!h || (guess_mode != LNOCC_GUESS_MP2 && guess_mode != LNOCC_GUESS_GIVEN && guess_mode != LNOCC_GUESS_MLP)) {
     lnocc::set_error("lnocc_ccsd: bad arguments");
     return LNOCC_EINVAL;
   }
   Frag& f = h->f;
   f.s = static_cast<cudaStream_t>(stream);
   f.use_workspace();
-  const int st = f.solve(guess_mode, t1_in, t2_in);
+  const int st = f.solve_with_fallback(guess_mode, t1_in, t2_in);
   const long long ov = 1LL * f.o * f.v;
   if (f.have_amps) {
     if (t1_out) cudaMemcpyAsync(t1_out, f.xcur, ov * 8, cudaMemcpyDeviceToDevice, f.s);
@@ -140,7 +141,7 @@ int lnocc_frag_info(const lnocc_frag* h, lnocc_info* info) {
   info->exec_flops = lnocc::gemm_stats().flops;
   info->gemm_launches = lnocc::gemm_stats().launches;
   info->device_bytes = f.device_bytes;
-  info->kernel_launches = lnocc::launch_counter();
+  info->kernel_launches = lnocc::launch_counter().load();
   info->t_triples_gemm_ms = f.t_gemm_ms;
   info->t_triples_ms = f.t_triples_ms;
   return LNOCC_OK;
@@ -183,6 +184,45 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
     lnocc::set_error("lnocc_debug_gemm: device wait timed out");
     return LNOCC_ETIMEOUT;
   }
+  return LNOCC_OK;
+}
+
+int lnocc_autotune(int mode, int* prev_mode) {
+  lnocc::set_error("");
+  if (mode > 2) {
+    lnocc::set_error("lnocc_autotune: mode must be 0, 1 or 2");
+    return LNOCC_EINVAL;
+  }
+  const int prev = lnocc::autotune_mode(mode < 0 ? -1 : mode);
+  if (prev_mode) *prev_mode = prev;
+  return LNOCC_OK;
+}
+
+int lnocc_autotune_save(const char* path) {
+  lnocc::set_error("");
+  if (!path || !lnocc::autotune_save(path)) {
+    lnocc::set_error("lnocc_autotune_save: cannot write the table");
+    return LNOCC_EINVAL;
+  }
+  return LNOCC_OK;
+}
+
+int lnocc_autotune_load(const char* path) {
+  lnocc::set_error("");
+  if (!path || !lnocc::autotune_load(path)) {
+    lnocc::set_error("lnocc_autotune_load: cannot read the table");
+    return LNOCC_EINVAL;
+  }
+  return LNOCC_OK;
+}
+
+int lnocc_autotune_stats(long long* entries, long long* hits, long long* misses, long long* tuned) {
+  long long s[4];
+  lnocc::autotune_stats(s);
+  if (entries) *entries = s[0];
+  if (hits) *hits = s[1];
+  if (misses) *misses = s[2];
+  if (tuned) *tuned = s[3];
   return LNOCC_OK;
 }
 

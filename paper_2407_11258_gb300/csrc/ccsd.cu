@@ -29,15 +29,31 @@ namespace lnocc {
 
 static inline Ax A(int n, long long s) { return Ax{n, s}; }
 
-void* Frag::alloc(size_t bytes, bool zero) {
+void* Frag::dev_alloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 256;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void Frag::dev_free(void* p) {
+  if (!p) return;
+  if (pool)
+    cudaFreeAsync(p, s);
+  else
+    cudaFree(p);
+}
+void* Frag::alloc(size_t bytes, bool zero) {
+  if (bytes == 0) bytes = 256;
+  void* p = dev_alloc(bytes);
+  if (!p) {
     oom = true;
     return nullptr;
   }
-  if (zero) cudaMemset(p, 0, bytes);
+  if (zero) cudaMemsetAsync(p, 0, bytes, s);
   allocs.push_back(p);
   device_bytes += static_cast<long long>(bytes);
   return p;
@@ -78,8 +94,10 @@ void Frag::prof_print(const char* title) {
 
 Frag::~Frag() {
   for (auto& m : marks) cudaEventDestroy(m.second);
-  for (void* p : allocs) cudaFree(p);
-  if (h_scal) cudaFreeHost(h_scal);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  for (void* p : allocs) dev_free(p);
+  if (h_scal && h_scal != h_ext) cudaFreeHost(h_scal);
 }
 
 Packed Frag::alloc_packed(int rows, int K, bool bf16) {
@@ -178,12 +196,15 @@ int Frag::build(const double* eps_in, const double* B_in) {
     derr = static_cast<double*>(alloc(dm * L * 8, true));
   }
   G = static_cast<double*>(alloc(64 * 8, true));
+  dctr = static_cast<int*>(alloc(16, true));
   coef = static_cast<double*>(alloc(8 * 8, true));
   dpart = static_cast<double*>(alloc(8 * 152 * 8, true));
   part = static_cast<double*>(alloc(152 * 32 * 8 * 4, true));
   scal = static_cast<double*>(alloc(16 * 8, true));
   dstatus = static_cast<int*>(alloc(16 * 4, true));
-  if (cudaMallocHost(&h_scal, 16 * 8) != cudaSuccess) {
+  if (h_ext) {
+    h_scal = h_ext;
+  } else if (cudaMallocHost(&h_scal, 16 * 8) != cudaSuccess) {
     h_scal = nullptr;
     oom = true;
   }
@@ -345,10 +366,10 @@ int Frag::build_consts(bool bf) {
                         PBvv, static_cast<int>(vv), out_rowmajor(gtmp, vv));
       launch_pack_vvvv(gtmp, a0, na, v, c.Vp, c.Vm, s);
     }
-    LN_CUDA(cudaStreamSynchronize(s));
+    if (!pool) LN_CUDA(cudaStreamSynchronize(s));
     // the chunk temporaries are released right away
     for (void* p : {static_cast<void*>(tmp), static_cast<void*>(gtmp), PBvv.p}) {
-      cudaFree(p);
+      dev_free(p);
       allocs.erase(std::find(allocs.begin(), allocs.end(), p));
     }
     device_bytes -= static_cast<long long>(kc) * per_k * 8 + static_cast<long long>(ac) * per_k * 8 +
@@ -563,6 +584,79 @@ double Frag::energy_of(const double* x) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// One CCSD iteration on stream s: residual and update, DIIS extrapolation into xcur, the energy of
+// xcur and the copy of (energy, squared update norm) to the pinned host buffer h_scal.
+void Frag::step(bool fp64_residual, bool use_diis) {
+  const long long L = 1LL * o * v + 1LL * o * o * v * v;
+  iterate(fp64_residual);
+  if (use_diis)
+    launch_diis_step(xnew, enew, dvec, derr, L, dm, dctr, dpart, G, coef, xcur, s);
+  else
+    cudaMemcpyAsync(xcur, xnew, L * 8, cudaMemcpyDeviceToDevice, s);
+  energy_of(xcur);
+  mark("diis_energy");
+  cudaMemcpyAsync(h_scal, scal, 16, cudaMemcpyDeviceToHost, s);
+}
+
+// Runs step() eagerly, or through the captured graph. The graph holds the FP64/mixed residual of the
+// fragment's own precision only (FP64 refinement iterations always run eagerly). Capture happens on a
+// private stream in thread-local mode, so other host threads may allocate meanwhile; if capture or
+// instantiation fails the solve continues eagerly.
+int Frag::launch_step(bool fp64_residual, bool use_diis, bool use_graph) {
+  if (!use_graph || fp64_residual || prof || graph_failed) {
+    step(fp64_residual, use_diis);
+    return LNOCC_OK;
+  }
+  if (!gexec) {
+    if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      graph_failed = true;
+      step(fp64_residual, use_diis);
+      return LNOCC_OK;
+    }
+    cudaStream_t user = s;
+    s = cap_stream;
+    const long long n0 = thread_launch_counter();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      step(false, use_diis);
+      ok = cudaStreamEndCapture(s, &g) == cudaSuccess && g;
+    }
+    s = user;
+    graph_kernels = thread_launch_counter() - n0;
+    // nothing ran during capture: take the captured launches back out of the counters
+    launch_counter().fetch_sub(graph_kernels, std::memory_order_relaxed);
+    thread_launch_counter() -= graph_kernels;
+    if (ok) ok = cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      gexec = nullptr;
+      graph_failed = true;
+      step(fp64_residual, use_diis);
+      return LNOCC_OK;
+    }
+  }
+  LN_CUDA(cudaGraphLaunch(gexec, s));
+  count_launch(graph_kernels);
+  return LNOCC_OK;
+}
+
+// The learned guess only changes where the iterations start: a solve from it that fails to converge
+// or turns non-finite is repeated from the MP2 guess (same convergence test), and the iterations of
+// both attempts are counted.
+int Frag::solve_with_fallback(int guess, const double* t1_in, const double* t2_in) {
+  mlp_used = mlp_fallback = false;
+  const int st = solve(guess, t1_in, t2_in);
+  if (guess != LNOCC_GUESS_MLP || st == LNOCC_OK || (st != LNOCC_ENOCONV && st != LNOCC_ENUMERIC)) return st;
+  const int first = n_iter;
+  mlp_fallback = true;
+  const int st2 = solve(LNOCC_GUESS_MP2, nullptr, nullptr);
+  n_iter += first;
+  return st2;
+}
+
 int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
   const long long ov = 1LL * o * v, L = ov + 1LL * o * o * v * v;
   cudaMemsetAsync(dstatus, 0, 16 * 4, s);
@@ -573,6 +667,29 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
     }
     LN_CUDA(cudaMemcpyAsync(xcur, t1_in, ov * 8, cudaMemcpyDeviceToDevice, s));
     LN_CUDA(cudaMemcpyAsync(xcur + ov, t2_in, (L - ov) * 8, cudaMemcpyDeviceToDevice, s));
+  } else if (guess == LNOCC_GUESS_MLP) {
+    if (!mlp) {
+      set_error("LNOCC_GUESS_MLP needs a model attached with lnocc_frag_set_mlp");
+      return LNOCC_EINVAL;
+    }
+    // t1 = 0, t2 = learned guess; a guess with any non-finite element is replaced by the MP2 guess
+    LN_CUDA(cudaMemsetAsync(xcur, 0, ov * 8, s));
+    const int st = mlp_guess(*mlp, o, v, t2mp2, eps, ovov, xcur + ov, dstatus, s);
+    if (st != LNOCC_OK) return st;
+    launch_finite(xcur + ov, L - ov, dstatus + 1, s);
+    int flag[2] = {0, 0};
+    LN_CUDA(cudaMemcpyAsync(flag, dstatus, 8, cudaMemcpyDeviceToHost, s));
+    LN_CUDA(cudaStreamSynchronize(s));
+    if (flag[0] != 0) {
+      set_error("learned-guess kernel: device wait timed out");
+      return LNOCC_ETIMEOUT;
+    }
+    mlp_used = flag[1] == 0;
+    mlp_fallback = !mlp_used;
+    if (!mlp_used) {
+      LN_CUDA(cudaMemsetAsync(dstatus, 0, 16 * 4, s));
+      LN_CUDA(cudaMemcpyAsync(xcur + ov, t2mp2, (L - ov) * 8, cudaMemcpyDeviceToDevice, s));
+    }
   } else {
     LN_CUDA(cudaMemsetAsync(xcur, 0, ov * 8, s));
     LN_CUDA(cudaMemcpyAsync(xcur + ov, t2mp2, (L - ov) * 8, cudaMemcpyDeviceToDevice, s));
@@ -584,30 +701,16 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
   converged = false;
   n_iter = 0;
   const bool use_diis = dm > 0 && !(opts.fault_inject & LNOCC_FAULT_ZERO_DIIS);
-  int nvec = 0, refine_left = mixed ? opts.n_refine : 0;
+  LN_CUDA(cudaMemsetAsync(dctr, 0, 16, s));
+  int refine_left = mixed ? opts.n_refine : 0;
   std::vector<double> hist_rms, hist_de;
   bool refining = false;
   const double tol_r = opts.conv_rms, tol_e = opts.conv_energy;
   for (int it = 1; it <= opts.max_iter; ++it) {
-    iterate(refining);
-    if (use_diis) {
-      const int slot = (it - 1) % dm;
-      cudaMemcpyAsync(dvec + slot * L, xnew, L * 8, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(derr + slot * L, enew, L * 8, cudaMemcpyDeviceToDevice, s);
-      nvec = std::min(nvec + 1, dm);
-      launch_diis_dots(enew, derr, L, nvec, dpart, G, slot, dm, s);
-      if (nvec >= 2) {
-        launch_diis_solve(G, nvec, dm, slot, coef, s);
-        launch_extrapolate(dvec, coef, nvec, L, xcur, s);
-      } else {
-        cudaMemcpyAsync(xcur, xnew, L * 8, cudaMemcpyDeviceToDevice, s);
-      }
-    } else {
-      cudaMemcpyAsync(xcur, xnew, L * 8, cudaMemcpyDeviceToDevice, s);
-    }
-    energy_of(xcur);
-    mark("diis_energy");
-    LN_CUDA(cudaMemcpyAsync(h_scal, scal, 16, cudaMemcpyDeviceToHost, s));
+    // the first iteration runs eagerly (first launches set kernel attributes); later ones replay a
+    // captured graph of the same launches when opts.graph is set
+    const int st_step = launch_step(refining, use_diis, opts.graph != 0 && it >= 2);
+    if (st_step != LNOCC_OK) return st_step;
     LN_CUDA(cudaStreamSynchronize(s));
     LN_CUDA(cudaGetLastError());
     prof_flush();

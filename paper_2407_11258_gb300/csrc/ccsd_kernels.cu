@@ -195,17 +195,34 @@ __global__ void k_mp2_amps(const double* ovov, const double* eps, double* t2, in
 }
 
 // dots[k] partials: sum_x e_new[x] * e_all[k][x] for k < m, one block row per k.
-__global__ void k_dots(const double* e_new, const double* e_all, long long len, int m, double* part, int nblk) {
+// DIIS bookkeeping lives on the device so that one CUDA graph serves every iteration:
+// ctr[0] = vectors pushed so far (cnt); the new vector goes to slot cnt % mmax and the subspace then
+// holds min(cnt + 1, mmax) vectors. k_diis_solve advances ctr[0] and records that count in ctr[1].
+__device__ __forceinline__ int diis_slot(const int* ctr, int mmax) { return ctr[0] % mmax; }
+__device__ __forceinline__ int diis_nvec(const int* ctr, int mmax) { return min(ctr[0] + 1, mmax); }
+
+__global__ void k_diis_push(const double* __restrict__ x, const double* __restrict__ e, double* __restrict__ xs,
+                            double* __restrict__ es, long long len, int mmax, const int* __restrict__ ctr) {
+  const long long off = static_cast<long long>(diis_slot(ctr, mmax)) * len;
+  GRID_STRIDE(idx, len) {
+    xs[off + idx] = x[idx];
+    es[off + idx] = e[idx];
+  }
+}
+__global__ void k_dots(const double* e_new, const double* e_all, long long len, int mmax, const int* ctr,
+                       double* part, int nblk) {
   const int k = blockIdx.y;
+  if (k >= diis_nvec(ctr, mmax)) return;
   double acc = 0.0;
   for (long long x = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; x < len;
        x += static_cast<long long>(gridDim.x) * blockDim.x)
     acc += e_new[x] * e_all[k * len + x];
   block_sum_store(acc, part + static_cast<long long>(k) * nblk);
 }
-
-__global__ void k_finish_dots(const double* part, int nblk, int m, double* G, int slot, int mmax) {
+__global__ void k_finish_dots(const double* part, int nblk, const int* ctr, double* G, int mmax) {
   const int k = blockIdx.x;
+  if (k >= diis_nvec(ctr, mmax)) return;
+  const int slot = diis_slot(ctr, mmax);
   double acc = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[static_cast<long long>(k) * nblk + i];
   const double tot = block_sum(acc);
@@ -214,11 +231,11 @@ __global__ void k_finish_dots(const double* part, int nblk, int m, double* G, in
     G[k * mmax + slot] = tot;
   }
 }
-
-// Pulay DIIS: solve [G 1; 1 0][c; l] = [0; 1] for the m stored vectors (Gaussian elimination with
-// partial pivoting in FP64, one thread). On a singular system the newest vector alone is used.
-__global__ void k_diis_solve(const double* G, int m, int mmax, int newest, double* coef) {
+__global__ void k_diis_solve(const double* G, int mmax, int* ctr, double* coef) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = diis_nvec(ctr, mmax), newest = diis_slot(ctr, mmax);
+  ctr[0] += 1;
+  ctr[1] = m;
   double A[9][10];
   const int n = m + 1;
   double scale = 0.0;
@@ -266,7 +283,8 @@ __global__ void k_diis_solve(const double* G, int m, int mmax, int newest, doubl
 }
 
 // out[x] = sum_k coef[k] * vecs[k][x]
-__global__ void k_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out) {
+__global__ void k_extrapolate(const double* vecs, const double* coef, const int* ctr, long long len, double* out) {
+  const int m = ctr[1];
   GRID_STRIDE(x, len) {
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc += coef[k] * vecs[k * len + x];
@@ -480,21 +498,15 @@ void launch_mp2_amps(const double* ovov, const double* eps, double* t2, int o, i
   count_launch();
   k_mp2_amps<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(ovov, eps, t2, o, v);
 }
-void launch_diis_dots(const double* e_new, const double* e_all, long long len, int m, double* part, double* G,
-                      int slot, int mmax, cudaStream_t s) {
+void launch_diis_step(const double* x_new, const double* e_new, double* xs, double* es, long long len, int mmax,
+                      int* ctr, double* part, double* G, double* coef, double* out, cudaStream_t s) {
   const int nblk = 152;
-  count_launch();
-  k_dots<<<dim3(nblk, m), kThreads, 0, s>>>(e_new, e_all, len, m, part, nblk);
-  count_launch();
-  k_finish_dots<<<m, kThreads, 0, s>>>(part, nblk, m, G, slot, mmax);
-}
-void launch_diis_solve(const double* G, int m, int mmax, int newest, double* coef, cudaStream_t s) {
-  count_launch();
-  k_diis_solve<<<1, 32, 0, s>>>(G, m, mmax, newest, coef);
-}
-void launch_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out, cudaStream_t s) {
-  count_launch();
-  k_extrapolate<<<grid_for(len), kThreads, 0, s>>>(vecs, coef, m, len, out);
+  count_launch(5);
+  k_diis_push<<<grid_for(len), kThreads, 0, s>>>(x_new, e_new, xs, es, len, mmax, ctr);
+  k_dots<<<dim3(nblk, mmax), kThreads, 0, s>>>(e_new, es, len, mmax, ctr, part, nblk);
+  k_finish_dots<<<mmax, kThreads, 0, s>>>(part, nblk, ctr, G, mmax);
+  k_diis_solve<<<1, 32, 0, s>>>(G, mmax, ctr, coef);
+  k_extrapolate<<<grid_for(len), kThreads, 0, s>>>(xs, coef, ctr, len, out);
 }
 void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s) {
   count_launch();

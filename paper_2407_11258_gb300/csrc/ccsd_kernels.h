@@ -18,10 +18,11 @@ int launch_energy(const double* t1, const double* t2, const double* ovov, double
                   cudaStream_t s);
 void launch_finish_sum(const double* part, int n, double* out, cudaStream_t s);
 void launch_mp2_amps(const double* ovov, const double* eps, double* t2, int o, int v, cudaStream_t s);
-void launch_diis_dots(const double* e_new, const double* e_all, long long len, int m, double* part, double* G,
-                      int slot, int mmax, cudaStream_t s);
-void launch_diis_solve(const double* G, int m, int mmax, int newest, double* coef, cudaStream_t s);
-void launch_extrapolate(const double* vecs, const double* coef, int m, long long len, double* out, cudaStream_t s);
+// One Pulay DIIS step with the subspace bookkeeping in device memory (ctr[2], zero before the first
+// step): push (x_new, e_new) into slot ctr[0] % mmax, update the overlap matrix G, solve for the
+// coefficients and write the extrapolated vector to out.
+void launch_diis_step(const double* x_new, const double* e_new, double* xs, double* es, long long len, int mmax,
+                      int* ctr, double* part, double* G, double* coef, double* out, cudaStream_t s);
 void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s);
 void launch_pair_dots(const double* tau, const double* L, int o, long long K, double* E, cudaStream_t s);
 void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s);

@@ -10,6 +10,11 @@
 
 namespace lnocc {
 
+struct Mlp;  // learned T2 guess model (mlp.cu)
+// learned guess t2_out[i][j][a][b] = t_MP2 + s_out g(features) over all o^2 v^2 amplitudes (mlp.cu)
+int mlp_guess(const Mlp& m, int o, int v, const double* t2mp2, const double* eps, const double* ovov, double* t2_out,
+              int* dstatus, cudaStream_t s);
+
 // Constant packed operands of the CCSD iteration for one precision.
 struct Consts {
   Packed kl_cd;  // (kc|ld): rows (k,l), K (c,d)          -> Y_ij^kl
@@ -30,12 +35,18 @@ struct Frag {
   bool mixed = true;
   cudaStream_t s = nullptr;
 
-  // allocation bookkeeping
+  // allocation bookkeeping. With `pool` set (the batch runtime), device memory comes from that
+  // stream-ordered pool on stream `s` and is returned with cudaFreeAsync (no device-wide
+  // synchronisation); otherwise cudaMalloc / cudaFree.
   std::vector<void*> allocs;
   long long device_bytes = 0;
   bool oom = false;
   bool scratch_overflow = false;
+  cudaMemPool_t pool = nullptr;
+  double* h_ext = nullptr;  // caller-owned pinned host buffer (16 doubles) used instead of cudaMallocHost
   void* alloc(size_t bytes, bool zero = false);
+  void* dev_alloc(size_t bytes);  // raw allocation in the fragment's memory mode (not tracked)
+  void dev_free(void* p);
   Packed alloc_packed(int rows, int K, bool bf16);
   ~Frag();
 
@@ -59,9 +70,18 @@ struct Frag {
   double* splitk = nullptr;  // split-K partials workspace
   size_t splitk_cap = 0;
   void use_workspace() { split_ws() = SplitWs{splitk, splitk_cap}; }
-  // DIIS
+  // DIIS (subspace counters on the device: dctr[0] vectors pushed, dctr[1] vectors in use)
   int dm = 0;
   double *dvec = nullptr, *derr = nullptr, *G = nullptr, *coef = nullptr, *dpart = nullptr;
+  int* dctr = nullptr;
+  // One CCSD iteration (residual, DIIS step, energy, copy of the convergence scalars to the host)
+  // captured as a CUDA graph on a private stream and replayed on `s`.
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_kernels = 0;
+  bool graph_failed = false;
+  void step(bool fp64_residual, bool use_diis);
+  int launch_step(bool fp64_residual, bool use_diis, bool use_graph);
   // reductions / status
   double *part = nullptr, *scal = nullptr, *h_scal = nullptr;
   int* dstatus = nullptr;
@@ -72,6 +92,7 @@ struct Frag {
   bool converged = false, have_amps = false;
   double flops_t = 0.0;
   double t_gemm_ms = 0.0, t_triples_ms = 0.0;  // device times of the last lnocc_triples
+  long long t_max_chunks = -1;  // > 0: run only ~this many W chunks spread over the (T) plan (autotuning; energy invalid)
 
   // optional per-step timing (environment LNOCC_PROFILE=1): events between named marks
   bool prof = false;
@@ -80,6 +101,11 @@ struct Frag {
   void mark(const char* name);
   void prof_flush();
   void prof_print(const char* title);
+
+  // learned guess (LNOCC_GUESS_MLP): the attached model, and what the last solve used
+  const Mlp* mlp = nullptr;
+  bool mlp_used = false, mlp_fallback = false;
+  int solve_with_fallback(int guess, const double* t1_in, const double* t2_in);
 
   int build(const double* eps_in, const double* B_in);
   int build_consts(bool bf);

@@ -9,6 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <map>
 #include <mutex>
 
 #include "internal.h"
@@ -17,12 +22,16 @@
 namespace lnocc {
 
 GemmStats& gemm_stats() {
-  static GemmStats s;
+  static thread_local GemmStats s;
   return s;
 }
 
-long long& launch_counter() {
-  static long long n = 0;
+std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> n{0};
+  return n;
+}
+long long& thread_launch_counter() {
+  static thread_local long long n = 0;
   return n;
 }
 
@@ -340,7 +349,7 @@ __global__ void k_splitk_reduce(const double* __restrict__ ws, int splits, int M
 }
 
 SplitWs& split_ws() {
-  static SplitWs w;
+  static thread_local SplitWs w;
   return w;
 }
 
@@ -672,14 +681,16 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 static int num_sms() {
-  static int n = 0;
-  if (n == 0) {
+  static std::atomic<int> n{0};
+  int v = n.load(std::memory_order_relaxed);
+  if (v == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 148;
+    n.store(v, std::memory_order_relaxed);
   }
-  return n;
+  return v;
 }
 
 // ---- host side: tensor maps
@@ -717,11 +728,10 @@ static bool make_map(CUtensorMap* map, const Packed& P, int box_rows) {
 
 template <int BN>
 static void set_smem_attr() {
-  static bool done = false;
-  if (!done) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
-    done = true;
-  }
+  });
 }
 
 // One launch: segment 1 is used when A1 != nullptr.
@@ -759,21 +769,192 @@ static void launch_tc(const Packed& A0, const Packed& B0, const Packed* A1, cons
   if (splits > 1) splitk_reduce(splits, args.M, args.N, args.C, s);
 }
 
+static int heuristic_bn(int N) {
+  return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : N <= 144 ? 144 : N <= 192 ? 192 : 256;
+}
+
+static void launch_bn(int bn, const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1,
+                      const TcArgs& a, int gridM, int nbatch, cudaStream_t s) {
+  switch (bn) {
+    case 32: launch_tc<32>(A0, B0, A1, B1, a, gridM, nbatch, s); break;
+    case 64: launch_tc<64>(A0, B0, A1, B1, a, gridM, nbatch, s); break;
+    case 128: launch_tc<128>(A0, B0, A1, B1, a, gridM, nbatch, s); break;
+    case 144: launch_tc<144>(A0, B0, A1, B1, a, gridM, nbatch, s); break;
+    case 192: launch_tc<192>(A0, B0, A1, B1, a, gridM, nbatch, s); break;
+    default: launch_tc<256>(A0, B0, A1, B1, a, gridM, nbatch, s); break;
+  }
+}
+
+// ---- tile autotuner ------------------------------------------------------------------------------
+// The N-width of the CTA tile (BN) decides the number of tiles (wave quantisation over the SMs), how
+// often each A tile is re-read, the TMEM columns and the pipeline depth. The fixed rule above takes
+// the narrowest BN that covers N; the tuner instead times every candidate on the real operands and
+// keeps the fastest per shape bucket (M and the K-block count in half-octaves, N in steps of 16,
+// one or two K segments). Timed runs write to a scratch copy of the output footprint with beta = 0,
+// so the call's real output is written once, by the chosen configuration, afterwards. Batched
+// (per-entry table) launches always use the fixed rule.
+namespace {
+struct TuneKey {
+  int seg, mb, nb, kb;
+  bool operator<(const TuneKey& o) const {
+    return seg != o.seg ? seg < o.seg : mb != o.mb ? mb < o.mb : nb != o.nb ? nb < o.nb : kb < o.kb;
+  }
+};
+struct Tuner {
+  std::mutex mu;
+  std::map<TuneKey, int> table;
+  std::atomic<int> mode{0};
+  long long hits = 0, misses = 0, tuned = 0;
+};
+Tuner& tuner() {
+  static Tuner t;
+  return t;
+}
+int half_octave(long long x) { return static_cast<int>(std::floor(2.0 * std::log2(static_cast<double>(std::max(x, 1LL))))); }
+TuneKey make_key(bool seg2, int M, int N, int nkb) { return TuneKey{seg2 ? 2 : 1, half_octave(M), (N + 15) / 16, half_octave(nkb)}; }
+
+// element range [lo, hi] that an OutMap touches for m < M, n < N (host mirror of out_moff / out_noff)
+void out_extent(const OutMap& C, int M, int N, long long* lo, long long* hi) {
+  auto moff = [&](int m) {
+    const int m0 = m % C.mdiv, mm = m / C.mdiv;
+    return (mm / C.mdiv1) * C.sm2 + (mm % C.mdiv1) * C.sm1 + static_cast<long long>(m0) * C.sm0;
+  };
+  auto noff = [&](int n) {
+    const int n0 = n % C.ndiv, nn = n / C.ndiv;
+    return (nn / C.ndiv1) * C.sn2 + (nn % C.ndiv1) * C.sn1 + static_cast<long long>(n0) * C.sn0;
+  };
+  long long mlo = LLONG_MAX, mhi = LLONG_MIN, nlo = LLONG_MAX, nhi = LLONG_MIN;
+  for (int m = 0; m < M; ++m) {
+    const long long x = moff(m);
+    mlo = std::min(mlo, x);
+    mhi = std::max(mhi, x);
+  }
+  for (int n = 0; n < N; ++n) {
+    const long long x = noff(n);
+    nlo = std::min(nlo, x);
+    nhi = std::max(nhi, x);
+  }
+  *lo = mlo + nlo;
+  *hi = mhi + nhi;
+}
+}  // namespace
+
+int autotune_mode(int mode) {
+  const int prev = tuner().mode.load();
+  if (mode >= 0) tuner().mode.store(mode);
+  return prev;
+}
+void autotune_stats(long long out[4]) {
+  Tuner& T = tuner();
+  std::lock_guard<std::mutex> lk(T.mu);
+  out[0] = static_cast<long long>(T.table.size());
+  out[1] = T.hits;
+  out[2] = T.misses;
+  out[3] = T.tuned;
+}
+bool autotune_save(const char* path) {
+  Tuner& T = tuner();
+  std::lock_guard<std::mutex> lk(T.mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return false;
+  std::fprintf(f, "# lnocc tile table: seg mbucket nbucket kbucket BN\n");
+  for (const auto& kv : T.table)
+    std::fprintf(f, "%d %d %d %d %d\n", kv.first.seg, kv.first.mb, kv.first.nb, kv.first.kb, kv.second);
+  return std::fclose(f) == 0;
+}
+bool autotune_load(const char* path) {
+  Tuner& T = tuner();
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  std::map<TuneKey, int> t;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    TuneKey k{};
+    int bn = 0;
+    if (std::sscanf(line, "%d %d %d %d %d", &k.seg, &k.mb, &k.nb, &k.kb, &bn) != 5) continue;
+    if (bn != 32 && bn != 64 && bn != 128 && bn != 144 && bn != 192 && bn != 256) continue;
+    t[k] = bn;
+  }
+  std::fclose(f);
+  std::lock_guard<std::mutex> lk(T.mu);
+  for (const auto& kv : t) T.table[kv.first] = kv.second;
+  return true;
+}
+
+static int tune_bn(const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1, const TcArgs& a,
+                   int gridM, cudaStream_t s, int fallback) {
+  long long lo = 0, hi = 0;
+  out_extent(a.C, a.M, a.N, &lo, &hi);
+  if (lo < 0 || hi < lo) return fallback;
+  const size_t esz = a.C.dst32 ? 4 : 8;
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, static_cast<size_t>(hi + 1) * esz) != cudaSuccess) {
+    cudaGetLastError();
+    return fallback;
+  }
+  TcArgs t = a;
+  t.C.beta = 0.0;
+  if (a.C.dst32) t.C.dst32 = static_cast<float*>(scratch);
+  else t.C.dst = static_cast<double*>(scratch);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = fallback;
+  float best_ms = 1e30f;
+  for (int bn : {32, 64, 128, 144, 192, 256}) {
+    if (bn != fallback && (bn / 2 >= std::max(a.N, 32) || (bn == 32 && a.N > 64))) continue;
+    launch_bn(bn, A0, B0, A1, B1, t, gridM, 1, s);  // warm-up (TMA descriptors, caches)
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      launch_bn(bn, A0, B0, A1, B1, t, gridM, 1, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_min = std::min(ms_min, ms);
+    }
+    if (ms_min < best_ms * 0.98f || (bn == fallback && ms_min <= best_ms)) {
+      best_ms = ms_min;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  return best;
+}
+
 static void dispatch_tc(const Packed& A0, const Packed& B0, const Packed* A1, const Packed* B1, const TcArgs& a,
                         int gridM, int nbatch, cudaStream_t s) {
-  const int N = a.N;
-  if (N <= 32)
-    launch_tc<32>(A0, B0, A1, B1, a, gridM, nbatch, s);
-  else if (N <= 64)
-    launch_tc<64>(A0, B0, A1, B1, a, gridM, nbatch, s);
-  else if (N <= 128)
-    launch_tc<128>(A0, B0, A1, B1, a, gridM, nbatch, s);
-  else if (N <= 144)
-    launch_tc<144>(A0, B0, A1, B1, a, gridM, nbatch, s);
-  else if (N <= 192)
-    launch_tc<192>(A0, B0, A1, B1, a, gridM, nbatch, s);
-  else
-    launch_tc<256>(A0, B0, A1, B1, a, gridM, nbatch, s);
+  int bn = heuristic_bn(a.N);
+  Tuner& T = tuner();
+  const int mode = T.mode.load(std::memory_order_relaxed);
+  if (mode != 0 && !a.batch) {
+    const TuneKey key = make_key(A1 != nullptr, a.M, a.N, a.nkb0 + a.nkb1);
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lk(T.mu);
+      auto it = T.table.find(key);
+      if (it != T.table.end()) {
+        bn = it->second;
+        found = true;
+        T.hits++;
+      } else {
+        T.misses++;
+      }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!found && mode == 2 && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      bn = tune_bn(A0, B0, A1, B1, a, gridM, s, bn);
+      std::lock_guard<std::mutex> lk(T.mu);
+      T.table[key] = bn;
+      T.tuned++;
+    }
+  }
+  launch_bn(bn, A0, B0, A1, B1, a, gridM, nbatch, s);
 }
 
 static TcArgs tc_args(int M, int N, int nkb0, int nkb1, const OutMap& C, int* dstatus) {

@@ -1,5 +1,6 @@
 // Internal (host-side) interfaces shared by the translation units of liblnocc.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -98,6 +99,7 @@ void gemm(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C
           int* dstatus);
 
 // Workspace for split-K partials (FP64 elements), provided by the caller of the contraction engine.
+// Per host thread: each thread drives its own fragment and stream.
 struct SplitWs {
   double* p = nullptr;
   size_t cap = 0;
@@ -108,10 +110,23 @@ struct GemmStats {
   long long launches = 0;
   double flops = 0.0;
 };
-GemmStats& gemm_stats();
-// Library-wide count of kernel launches issued by the host wrappers (monotonic).
-long long& launch_counter();
-inline void count_launch(long long n = 1) { launch_counter() += n; }
+GemmStats& gemm_stats();  // per host thread
+// Library-wide count of kernel launches issued by the host wrappers (monotonic, all threads), and the
+// calling thread's own count (used to count the kernels a captured CUDA graph holds).
+std::atomic<long long>& launch_counter();
+long long& thread_launch_counter();
+inline void count_launch(long long n = 1) {
+  launch_counter().fetch_add(n, std::memory_order_relaxed);
+  thread_launch_counter() += n;
+}
+
+// Tile autotuner of the tcgen05 GEMM (gemm.cu). mode 0: fixed BN rule; 1: use the table (fixed rule
+// on a miss); 2: time the candidates for shapes missing from the table (synchronous; not while the
+// stream is being captured). autotune_mode(-1) only reads the mode.
+int autotune_mode(int mode);
+void autotune_stats(long long out[4]);  // entries, hits, misses, shapes tuned
+bool autotune_save(const char* path);
+bool autotune_load(const char* path);
 
 void set_error(const std::string& msg);
 

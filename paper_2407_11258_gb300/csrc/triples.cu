@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "ccsd_kernels.h"
@@ -134,11 +135,14 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
 // s = 1/sqrt(-Delta) and -Delta = d_i + d_j + d_k, d_m = (e_a + e_b + e_c)/3 - e_m > 0 evaluated in FP64
 // (a sum of positive terms: no cancellation when it is rounded to Real). Threads then run over (j, k)
 // and every distinct ordering of (a, b, c); the i-sums are accumulated in Real and the block sum in FP64.
-template <typename TW, typename Real>
+template <typename TW, typename Real, int NLO>
 __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
                                   const double* __restrict__ eps, const double* __restrict__ t1,
-                                  const double* __restrict__ ovov, const double* __restrict__ U, int nlo,
+                                  const double* __restrict__ ovov, const double* __restrict__ U, int nlo_rt,
                                   double* __restrict__ out) {
+  // NLO: number of fragment LO columns of U, fixed at compile time (0 = canonical energy only);
+  // U is zero-padded to NLO columns by the host, so nlo_rt (the caller's count) is not needed here
+  (void)nlo_rt;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int slot = blockIdx.y, a = blockIdx.x;
   const int c = c0 + slot;
@@ -173,7 +177,7 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
     tc[y] = static_cast<Real>(t1[y * v + c]);
     dm[y] = static_cast<Real>(ex3 - eps[y]);
   }
-  for (int idx = threadIdx.x; idx < o * nlo; idx += blockDim.x) Us[idx] = static_cast<Real>(U[idx]);
+  for (int idx = threadIdx.x; idx < o * NLO; idx += blockDim.x) Us[idx] = static_cast<Real>(U[idx]);
   __syncthreads();
   const TW* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
   // W is stored [i][k][j] (j fastest): read it in that order (coalesced)
@@ -214,24 +218,22 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
       const int base1 = j * SS(p2) + k * SS(p0), si1 = SS(p1);
       const int base2 = j * SS(p0) + k * SS(p1), si2 = SS(p2);
       const int base3 = j * SS(p1) + k * SS(p0), si3 = SS(p2);
-      Real acc = 0, zu[8], yu[8];
+      Real acc = 0, zu[NLO > 0 ? NLO : 1], yu[NLO > 0 ? NLO : 1];
 #pragma unroll
-      for (int al = 0; al < 8; ++al) zu[al] = yu[al] = 0;
+      for (int al = 0; al < NLO; ++al) zu[al] = yu[al] = 0;
       for (int i = 0; i < o; ++i) {
         const Real z = 4 * sw[base0 + i * si0] + sw[base1 + i * si1] + sw[base2 + i * si2];
         const Real y = sv[base0 + i * si0] - sv[base3 + i * si3];
         acc += z * y;
 #pragma unroll
-        for (int al = 0; al < 8; ++al)
-          if (al < nlo) {
-            zu[al] += Us[i * nlo + al] * z;
-            yu[al] += Us[i * nlo + al] * y;
-          }
+        for (int al = 0; al < NLO; ++al) {
+          zu[al] += Us[i * NLO + al] * z;
+          yu[al] += Us[i * NLO + al] * y;
+        }
       }
       r_can += acc;
 #pragma unroll
-      for (int al = 0; al < 8; ++al)
-        if (al < nlo) r_frag += zu[al] * yu[al];
+      for (int al = 0; al < NLO; ++al) r_frag += zu[al] * yu[al];
     }
   }
   double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
@@ -319,17 +321,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   // ---- operands (packed once per call)
   std::vector<void*> mine;
   auto tmp_alloc = [&](size_t bytes) -> void* {
-    void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(bytes, 256)) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    mine.push_back(p);
+    void* p = dev_alloc(std::max<size_t>(bytes, 256));
+    if (p) mine.push_back(p);
     return p;
   };
   auto cleanup = [&]() {
     cudaStreamSynchronize(s);
-    for (void* p : mine) cudaFree(p);
+    for (void* p : mine) dev_free(p);
   };
   auto mk = [&](int rows, int K) -> Packed {
     Packed P;
@@ -442,15 +440,66 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 
   const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
   const bool staged = 2LL * sblk * wsz + (3LL * o * (o + 1) + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
-  const size_t esmem =
-      2 * sblk * wsz + (3 * static_cast<size_t>(o) * (o + 1) + 4 * o + static_cast<size_t>(o) * std::max(nlo, 1)) * wsz;
+  // (the staged kernel reads U padded to its compile-time LO count)
+  const size_t esmem = 2 * sblk * wsz + (3 * static_cast<size_t>(o) * (o + 1) + 4 * o + static_cast<size_t>(o) * 8) * wsz;
+  // the energy kernel is compiled for 0, 1, 2, 4 or 8 LOs; U is zero-padded to the next size
+  const int nlo_t = nlo == 0 ? 0 : nlo <= 1 ? 1 : nlo <= 2 ? 2 : nlo <= 4 ? 4 : 8;
+  double* dUp = nullptr;
+  if (nlo_t > 0) {
+    dUp = static_cast<double*>(tmp_alloc(static_cast<size_t>(o) * nlo_t * 8));
+    if (!dUp) {
+      cleanup();
+      set_error("lnocc_triples: device allocation failed (U)");
+      return LNOCC_ENOMEM;
+    }
+    cudaMemsetAsync(dUp, 0, static_cast<size_t>(o) * nlo_t * 8, s);
+    cudaMemcpy2DAsync(dUp, nlo_t * 8, U, nlo * 8, nlo * 8, o, cudaMemcpyDeviceToDevice, s);
+  }
+  auto energy_launch = [&](const void* Wp, long long Sc, int b, int c0, int na, int nc, double* part) {
+    dim3 grid(na, nc);
+    count_launch();
+#define LN_E(T, R, K)                                                                                             \
+  k_t_energy_staged<T, R, K><<<grid, 256, esmem, s>>>(static_cast<const T*>(Wp), Sc, b, c0, o, v, eps, t1, ovov, \
+                                                      dUp, nlo_t, part)
+    if (bf) {
+      switch (nlo_t) {
+        case 0: LN_E(float, float, 0); break;
+        case 1: LN_E(float, float, 1); break;
+        case 2: LN_E(float, float, 2); break;
+        case 4: LN_E(float, float, 4); break;
+        default: LN_E(float, float, 8); break;
+      }
+    } else {
+      switch (nlo_t) {
+        case 0: LN_E(double, double, 0); break;
+        case 1: LN_E(double, double, 1); break;
+        case 2: LN_E(double, double, 2); break;
+        case 4: LN_E(double, double, 4); break;
+        default: LN_E(double, double, 8); break;
+      }
+    }
+#undef LN_E
+  };
   if (staged) {
-    if (bf)
-      cudaFuncSetAttribute(k_t_energy_staged<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(esmem));
-    else
-      cudaFuncSetAttribute(k_t_energy_staged<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(esmem));
+    // The attribute is per kernel and process-wide: set it once to the largest size the staged
+    // kernel is ever launched with (the 200 KB cap above), so that concurrent calls on fragments of
+    // other sizes never lower it under one another's launches.
+    static std::once_flag once;
+    std::call_once(once, [] {
+      auto attr = [](const void* fn) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      };
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 1>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 2>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 4>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 8>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 4>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 8>));
+    });
   } else if (bf) {
     cleanup();
     set_error("lnocc_triples: nocc too large for the staged (T) energy kernel in this build");
@@ -462,7 +511,11 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     return m;
   };
   const int o2 = static_cast<int>(oo);
+  // tuning passes (t_max_chunks > 0) visit about t_max_chunks chunks spread over the plan
+  const size_t chunk_stride = t_max_chunks > 0 ? std::max<size_t>(1, plan.size() / t_max_chunks) : 1;
+  size_t chunk_idx = 0;
   for (const Chunk& ch : plan) {
+    if (chunk_idx++ % chunk_stride != 0) continue;
     const int b = ch.b, c0 = ch.c0, nc = ch.nc;
     const int na = b + 1, Ma = na * o, Ma2 = na * o2;
     const long long Sc = 1LL * na * ooo;  // W stride of c
@@ -516,16 +569,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     }
     cudaEventRecord(e1, s);
     gev.emplace_back(e0, e1);
-    count_launch();
-    if (bf)
-      k_t_energy_staged<float, float><<<dim3(na, nc), 256, esmem, s>>>(
-          static_cast<const float*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo, tpart + 2 * ch.part);
-    else if (staged)
-      k_t_energy_staged<double, double><<<dim3(na, nc), 256, esmem, s>>>(
-          static_cast<const double*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo, tpart + 2 * ch.part);
-    else
+    if (staged) {
+      energy_launch(W, Sc, b, c0, na, nc, tpart + 2 * ch.part);
+    } else {
+      count_launch();
       k_t_energy<<<dim3(na, nc), 128, 0, s>>>(static_cast<const double*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo,
                                               tpart + 2 * ch.part);
+    }
   }
   k_t_finish<<<1, 1024, 0, s>>>(tpart, nblk_total, scal + 4);
   cudaMemcpyAsync(h_scal + 4, scal + 4, 16, cudaMemcpyDeviceToHost, s);

@@ -14,21 +14,27 @@ LIB_PATH = os.path.join(PKG, "liblnocc.so")
 
 LNOCC_OK, LNOCC_EINVAL, LNOCC_ENOMEM, LNOCC_ENOCONV, LNOCC_ENUMERIC, LNOCC_ETIMEOUT, LNOCC_ECUDA = range(7)
 LNOCC_PREC_FP64, LNOCC_PREC_MIXED = 0, 1
-LNOCC_GUESS_MP2, LNOCC_GUESS_GIVEN = 0, 1
+LNOCC_GUESS_MP2, LNOCC_GUESS_GIVEN, LNOCC_GUESS_MLP = 0, 1, 2
 LNOCC_FAULT_NAN_INPUT, LNOCC_FAULT_ZERO_DIIS = 1, 2
 
 ERR_NAMES = {0: "LNOCC_OK", 1: "LNOCC_EINVAL", 2: "LNOCC_ENOMEM", 3: "LNOCC_ENOCONV", 4: "LNOCC_ENUMERIC",
              5: "LNOCC_ETIMEOUT", 6: "LNOCC_ECUDA"}
 
+LNOCC_ORDER_LPT, LNOCC_ORDER_INPUT = 0, 1
+
 EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragment_energy", "lnocc_triples",
            "lnocc_debug_gemm", "lnocc_gemm_noalloc", "lnocc_frag_info", "lnocc_free_fragment", "lnocc_last_error",
-           "lnocc_version"]
+           "lnocc_version", "lnocc_default_batch_opts", "lnocc_solve_batch", "lnocc_autotune", "lnocc_autotune_save",
+           "lnocc_autotune_load", "lnocc_autotune_stats", "lnocc_mlp_nparams", "lnocc_mlp_create", "lnocc_mlp_free",
+           "lnocc_mlp_get", "lnocc_mlp_set_norm", "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step",
+           "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("diis_space", ctypes.c_int),
                 ("n_refine", ctypes.c_int), ("conv_rms", ctypes.c_double), ("conv_energy", ctypes.c_double),
-                ("fault_inject", ctypes.c_int), ("verbose", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("fault_inject", ctypes.c_int), ("verbose", ctypes.c_int), ("graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Info(ctypes.Structure):
@@ -39,6 +45,25 @@ class Info(ctypes.Structure):
                 ("gemm_launches", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("t_triples_gemm_ms", ctypes.c_double),
                 ("t_triples_ms", ctypes.c_double)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int), ("nlo", ctypes.c_int),
+                ("eps", ctypes.c_void_p), ("B", ctypes.c_void_p), ("U_frag", ctypes.c_void_p)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int), ("triples", ctypes.c_int), ("order", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("mem_budget_gb", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_iter", ctypes.c_int), ("worker", ctypes.c_int), ("order", ctypes.c_int),
+                ("e_mp2", ctypes.c_double), ("e_ccsd", ctypes.c_double), ("e_mp2_frag", ctypes.c_double),
+                ("e_ccsd_frag", ctypes.c_double), ("e_t", ctypes.c_double), ("e_t_frag", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_end_ms", ctypes.c_double), ("model_flops", ctypes.c_double),
+                ("device_bytes", ctypes.c_longlong), ("cost_estimate", ctypes.c_double),
+                ("bytes_estimate", ctypes.c_longlong)]
 
 
 class LnoccError(RuntimeError):
@@ -69,6 +94,35 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lnocc_gemm_noalloc.argtypes = [I, I, I, I, P, P, P, P]
     lib.lnocc_frag_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lnocc_free_fragment.argtypes = [P]
+    lib.lnocc_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
+    lib.lnocc_default_batch_opts.restype = None
+    lib.lnocc_solve_batch.argtypes = [I, ctypes.POINTER(BatchItem), ctypes.POINTER(Opts), ctypes.POINTER(BatchOpts),
+                                      ctypes.POINTER(BatchResult), P]
+    lib.lnocc_solve_batch.restype = I
+    LL = ctypes.POINTER(ctypes.c_longlong)
+    lib.lnocc_autotune.argtypes = [I, ctypes.POINTER(I)]
+    lib.lnocc_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.lnocc_autotune_load.argtypes = [ctypes.c_char_p]
+    lib.lnocc_autotune_stats.argtypes = [LL, LL, LL, LL]
+    for name in ("lnocc_autotune", "lnocc_autotune_save", "lnocc_autotune_load", "lnocc_autotune_stats"):
+        getattr(lib, name).restype = I
+    F = ctypes.c_float
+    lib.lnocc_mlp_nparams.argtypes = []
+    lib.lnocc_mlp_create.argtypes = [ctypes.POINTER(F), ctypes.POINTER(P)]
+    lib.lnocc_mlp_free.argtypes = [P]
+    lib.lnocc_mlp_get.argtypes = [P, ctypes.POINTER(F), ctypes.POINTER(D)]
+    lib.lnocc_mlp_set_norm.argtypes = [P, ctypes.POINTER(D)]
+    lib.lnocc_mlp_samples.argtypes = [P, I, P, P, P, P]
+    lib.lnocc_mlp_fit_norm.argtypes = [P, I, P, P, P]
+    lib.lnocc_mlp_train_step.argtypes = [P, I, P, P, F, ctypes.POINTER(D), P]
+    lib.lnocc_mlp_forward.argtypes = [P, I, I, P, P, P]
+    lib.lnocc_mlp_grad.argtypes = [P, I, I, P, P, P, ctypes.POINTER(D), P]
+    lib.lnocc_mlp_guess.argtypes = [P, P, P, P]
+    lib.lnocc_frag_set_mlp.argtypes = [P, P]
+    for name in ("lnocc_mlp_nparams", "lnocc_mlp_create", "lnocc_mlp_free", "lnocc_mlp_get", "lnocc_mlp_set_norm",
+                 "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step", "lnocc_mlp_forward",
+                 "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp"):
+        getattr(lib, name).restype = I
     lib.lnocc_last_error.restype = ctypes.c_char_p
     lib.lnocc_version.restype = ctypes.c_char_p
     for name in ("lnocc_build_ints", "lnocc_ccsd", "lnocc_fragment_energy", "lnocc_triples", "lnocc_debug_gemm",
@@ -78,14 +132,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     return lib
 
 
-def _ptr(x):
+def _ptr(x, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (float64 unless dtype names another torch dtype)."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
     import torch
-    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    want = dtype if dtype is not None else torch.float64
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == want and x.is_contiguous()):
+        raise TypeError(f"expected a contiguous {want} CUDA tensor")
     return x.data_ptr()
 
 
@@ -179,3 +235,125 @@ def lnocc_gemm_noalloc(precision, A, B, C, stream=None):
     N = B.shape[0]
     _check(load().lnocc_gemm_noalloc(precision, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
     return C
+
+
+def default_batch_opts(**kw) -> BatchOpts:
+    b = BatchOpts()
+    load().lnocc_default_batch_opts(ctypes.byref(b))
+    for k, v in kw.items():
+        setattr(b, k, v)
+    return b
+
+
+def lnocc_solve_batch(frags, opts=None, bopts=None, stream=None, allow_noconv=False):
+    """Solve independent fragments. frags: sequence of (nocc, nvir, naux, eps, B, U_frag or None), device
+    tensors as for lnocc_build_ints. Returns (status, [BatchResult per fragment])."""
+    n = len(frags)
+    items = (BatchItem * max(n, 1))()
+    for k, (o, v, q, eps, B, U) in enumerate(frags):
+        items[k] = BatchItem(o, v, q, int(U.shape[1]) if U is not None else 0, _ptr(eps), _ptr(B), _ptr(U))
+    res = (BatchResult * max(n, 1))()
+    code = load().lnocc_solve_batch(n, items, ctypes.byref(opts) if opts else None,
+                                    ctypes.byref(bopts) if bopts else None, res, _stream(stream))
+    _check(code, (LNOCC_OK, LNOCC_ENOCONV) if allow_noconv else (LNOCC_OK,))
+    return code, [res[k] for k in range(n)]
+
+
+def lnocc_autotune(mode=-1):
+    """Set the tile autotuner mode (0 fixed rule, 1 table, 2 tune misses); returns the previous mode."""
+    prev = ctypes.c_int(0)
+    _check(load().lnocc_autotune(mode, ctypes.byref(prev)))
+    return prev.value
+
+
+def lnocc_autotune_save(path):
+    _check(load().lnocc_autotune_save(os.fsencode(path)))
+
+
+def lnocc_autotune_load(path):
+    _check(load().lnocc_autotune_load(os.fsencode(path)))
+
+
+def lnocc_autotune_stats():
+    """Returns dict(entries, hits, misses, tuned)."""
+    v = [ctypes.c_longlong(0) for _ in range(4)]
+    _check(load().lnocc_autotune_stats(*[ctypes.byref(x) for x in v]))
+    return dict(zip(("entries", "hits", "misses", "tuned"), (x.value for x in v)))
+
+
+# ------------------------------------------------------------------------------ learned T2 guess
+class Mlp:
+    """Owns an lnocc_mlp handle (parameters, Adam state and workspace on the device)."""
+
+    def __init__(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != load().lnocc_mlp_nparams():
+            raise ValueError(f"expected {load().lnocc_mlp_nparams()} parameters, got {p.size}")
+        self.h = ctypes.c_void_p()
+        _check(load().lnocc_mlp_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(self.h)))
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().lnocc_mlp_free(self.h)
+            self.h = None
+
+    def get(self):
+        """(params float32[nparams], norm float64[17]) as numpy arrays."""
+        import numpy as np
+        p = np.zeros(load().lnocc_mlp_nparams(), dtype=np.float32)
+        nrm = np.zeros(17)
+        _check(load().lnocc_mlp_get(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                    nrm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return p, nrm
+
+    def set_norm(self, norm):
+        import numpy as np
+        nrm = np.ascontiguousarray(norm, dtype=np.float64)
+        _check(load().lnocc_mlp_set_norm(self.h, nrm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def fit_norm(self, X, dt, stream=None):
+        import torch
+        _check(load().lnocc_mlp_fit_norm(self.h, X.shape[0], _ptr(X, torch.float32), _ptr(dt, torch.float32),
+                                         _stream(stream)))
+
+    def train_step(self, X, dt, lr, stream=None):
+        import torch
+        loss = ctypes.c_double(0.0)
+        _check(load().lnocc_mlp_train_step(self.h, X.shape[0], _ptr(X, torch.float32), _ptr(dt, torch.float32),
+                                           lr, ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def forward(self, X, precision=LNOCC_PREC_FP64, stream=None):
+        import torch
+        y = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        _check(load().lnocc_mlp_forward(self.h, precision, X.shape[0], _ptr(X, torch.float32), _ptr(y),
+                                        _stream(stream)))
+        return y
+
+    def grad(self, X, dt, precision=LNOCC_PREC_FP64, stream=None):
+        import torch
+        g = torch.empty(load().lnocc_mlp_nparams(), dtype=torch.float64, device=X.device)
+        loss = ctypes.c_double(0.0)
+        _check(load().lnocc_mlp_grad(self.h, precision, X.shape[0], _ptr(X, torch.float32), _ptr(dt, torch.float32),
+                                     _ptr(g), ctypes.byref(loss), _stream(stream)))
+        return loss.value, g
+
+
+def lnocc_mlp_samples(frag: Fragment, idx, X, dt=None, stream=None):
+    """Features X [n][8] (float32) and targets dt [n] (float32) of flat amplitude indices idx (int64)."""
+    import torch
+    _check(load().lnocc_mlp_samples(frag.h, idx.shape[0], _ptr(idx, torch.int64), _ptr(X, torch.float32),
+                                    _ptr(dt, torch.float32), _stream(stream)))
+
+
+def lnocc_mlp_guess(frag: Fragment, mlp: Mlp, t2_out, stream=None):
+    _check(load().lnocc_mlp_guess(frag.h, mlp.h, _ptr(t2_out), _stream(stream)))
+    return t2_out
+
+
+def lnocc_frag_set_mlp(frag: Fragment, mlp):
+    _check(load().lnocc_frag_set_mlp(frag.h, mlp.h if mlp is not None else None))

@@ -185,3 +185,54 @@ def triples_large(seed: int = 4000, scaled: bool = False) -> Fragment:
     if scaled:
         return make_fragment(12, 96, 320, seed + 1, decay=20.0, frag=(0,))
     return make_fragment(32, 480, 1600, seed, decay=20.0, frag=(0,))
+
+
+def batch_fragment_device(f: int, device, nfrag: int = 128, seed: int = 3000):
+    """Fragment f of the uneven batch at full size with B drawn on the device (fragment_device): the CPU
+    stream needs minutes for the ~88 GB batch. Orbital energies and U come from the same splitmix64
+    streams as batch_fragment. Returns (nocc, nvir, naux, eps, B, U_frag), U_frag the first LO."""
+    o, v, q, small = batch_shapes(nfrag, seed)[f]
+    return fragment_device(o, v, q, small, seed + f, device)
+
+
+def mlp_shapes(nfrag: int, seed: int = 5000):
+    """Learned-guess fragments: nocc U{8..16}, nvir U{96..240}, naux = 4*nvir; odd index = small gap."""
+    st = Stream(seed, 7)
+    no = st.integers(nfrag, 8, 16)
+    nv = st.integers(nfrag, 96, 240)
+    return [(int(no[f]), int(nv[f]), int(4 * nv[f]), bool(f % 2)) for f in range(nfrag)]
+
+
+def fragment_device(o: int, v: int, q: int, small: bool, seed: int, device, frag=(0,)):
+    """(nocc, nvir, naux, eps, B, U_frag) with eps / U from splitmix64 streams and B drawn on the device with
+    torch's seeded generator (same distribution as df_tensor, decay length 20)."""
+    import torch
+    n = o + v
+    st_e, st_u = Stream(seed, 1), Stream(seed, 3)
+    eps = small_gap_energies(st_e, o, v) if small else orbital_energies(st_e, o, v, (-1.2, -0.4), (0.3, 4.0))
+    U = orthogonal(st_u, o)[:, list(frag)].copy()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    B = torch.randn(q, n, n, generator=gen, device=device, dtype=torch.float64)
+    B = torch.triu(B) + torch.triu(B, 1).transpose(1, 2)
+    idx = torch.arange(n, device=device, dtype=torch.float64)
+    B *= (0.3 / np.sqrt(q)) * torch.exp(-(idx[:, None] - idx[None, :]).abs() / 20.0)
+    return (o, v, q, torch.tensor(eps, device=device), B.contiguous(), torch.tensor(U, device=device))
+
+
+def mlp_fragment_device(k: int, device, seed: int = 5000, nfrag: int = 2256, scale_shape=None):
+    """Fragment k of the learned-guess set (k < 2000: training, the rest held out)."""
+    o, v, q, small = mlp_shapes(nfrag, seed)[k]
+    if scale_shape is not None:
+        o, v = scale_shape(o, v)
+        q = 4 * v
+    return fragment_device(o, v, q, small, seed + 1 + k, device)
+
+
+def mlp_init(seed: int = 5100, hidden: int = 128) -> np.ndarray:
+    """Initial MLP parameters in the layout W1[H][8], b1[H], W2[H][H], b2[H], w3[H], b3[1]:
+    weights N(0, 1/fan_in), biases 0."""
+    st = Stream(seed, 15)
+    parts = [st.normal(hidden * 8) / np.sqrt(8.0), np.zeros(hidden), st.normal(hidden * hidden) / np.sqrt(hidden),
+             np.zeros(hidden), st.normal(hidden) / np.sqrt(hidden), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_options_and_version(lib):
     o = lnocc.default_opts()
     assert o.precision == lnocc.LNOCC_PREC_MIXED and o.max_iter == 100 and o.diis_space == 8
-    assert o.conv_rms == 1e-8 and o.conv_energy == 1e-10
+    assert o.conv_rms == 1e-8 and o.conv_energy == 1e-10 and o.graph == 1
     assert b"sm_103a" in lib.lnocc_version()
 
 
@@ -55,24 +55,64 @@ def test_argument_validation_needs_no_gpu(lib):
 
 
 def test_struct_layouts_match_header(tmp_path):
-    """ctypes mirrors of lnocc_opts / lnocc_info have the C compiler's size and field offsets."""
+    """ctypes mirrors of the header's structs have the C compiler's size and field offsets."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields_o = [f[0] for f in lnocc.Opts._fields_]
-    fields_i = [f[0] for f in lnocc.Info._fields_]
-    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "lnocc.h"', "int main(void){",
-           'printf("%zu %zu\\n", sizeof(lnocc_opts), sizeof(lnocc_info));']
-    src += [f'printf("%zu\\n", offsetof(lnocc_opts, {f}));' for f in fields_o]
-    src += [f'printf("%zu\\n", offsetof(lnocc_info, {f}));' for f in fields_i]
+    mirrors = [("lnocc_opts", lnocc.Opts), ("lnocc_info", lnocc.Info), ("lnocc_batch_item", lnocc.BatchItem),
+               ("lnocc_batch_opts", lnocc.BatchOpts), ("lnocc_batch_result", lnocc.BatchResult)]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "lnocc.h"', "int main(void){"]
+    for cname, py in mirrors:
+        src.append(f'printf("%zu\\n", sizeof({cname}));')
+        src += [f'printf("%zu\\n", offsetof({cname}, {f[0]}));' for f in py._fields_]
     src += ["return 0;}"]
     (tmp_path / "t.c").write_text("\n".join(src))
     exe = tmp_path / "t"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(tmp_path / "t.c"), "-o", str(exe)], check=True)
-    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    assert int(out[0]) == ctypes.sizeof(lnocc.Opts) and int(out[1]) == ctypes.sizeof(lnocc.Info)
-    offs = [int(x) for x in out[2:]]
-    assert offs[: len(fields_o)] == [getattr(lnocc.Opts, f).offset for f in fields_o]
-    assert offs[len(fields_o):] == [getattr(lnocc.Info, f).offset for f in fields_i]
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for _, py in mirrors:
+        want.append(ctypes.sizeof(py))
+        want += [getattr(py, f[0]).offset for f in py._fields_]
+    assert out == want
+
+
+def test_batch_argument_validation_needs_no_gpu(lib):
+    """lnocc_solve_batch rejects bad items and options on the host before touching the device."""
+    b = lnocc.default_batch_opts()
+    assert b.workers == 0 and b.triples == 1 and b.order == lnocc.LNOCC_ORDER_LPT and b.mem_budget_gb == 0.0
+    res = (lnocc.BatchResult * 1)()
+    assert lib.lnocc_solve_batch(0, None, None, None, None, None) == lnocc.LNOCC_OK
+    assert lib.lnocc_solve_batch(-1, None, None, None, None, None) == lnocc.LNOCC_EINVAL
+    items = (lnocc.BatchItem * 1)()
+    items[0] = lnocc.BatchItem(4, 20, 80, 0, 1, 1, None)
+    bad = lnocc.default_batch_opts(workers=99)
+    assert lib.lnocc_solve_batch(1, items, None, ctypes.byref(bad), res, None) == lnocc.LNOCC_EINVAL
+    assert b"batch options" in lib.lnocc_last_error()
+    items[0] = lnocc.BatchItem(4, 20, 80, 2, 1, 1, None)  # nlo > 0 without U_frag
+    assert lib.lnocc_solve_batch(1, items, None, None, res, None) == lnocc.LNOCC_EINVAL
+    assert b"bad item 0" in lib.lnocc_last_error()
+
+
+def test_autotune_table_io_needs_no_gpu(lib, tmp_path):
+    """Mode switch, text table load (merge, invalid lines skipped) and save round trip, host only."""
+    prev = lnocc.lnocc_autotune(1)
+    try:
+        assert lnocc.lnocc_autotune(-1) == 1
+        with pytest.raises(lnocc.LnoccError):
+            lnocc.lnocc_autotune(3)
+        n0 = lnocc.lnocc_autotune_stats()["entries"]
+        src = tmp_path / "tiles.txt"
+        src.write_text("# comment\n1 20 9 14 128\n2 22 16 10 256\n1 20 9 15 100\nnot a line\n")
+        lnocc.lnocc_autotune_load(str(src))
+        assert lnocc.lnocc_autotune_stats()["entries"] == n0 + 2  # BN=100 is not a kernel: skipped
+        out = tmp_path / "saved.txt"
+        lnocc.lnocc_autotune_save(str(out))
+        rows = [r for r in out.read_text().splitlines() if not r.startswith("#")]
+        assert "1 20 9 14 128" in rows and "2 22 16 10 256" in rows
+        with pytest.raises(lnocc.LnoccError):
+            lnocc.lnocc_autotune_load(str(tmp_path / "missing.txt"))
+    finally:
+        lnocc.lnocc_autotune(prev)
