@@ -8,6 +8,7 @@ in for the paper's diamond fragment (seeded generator in paper_2407_11258_gb300/
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-fp64] [--no-cpu]
     python bench.py --workload batch [--nfrag 128] [--workers 0] [--autotune 1] [--steps 1] [--warmup 1]
     python bench.py --workload mlp [--ntrain 256] [--nheld 64] [--train-steps 2000] [--mlp-precision mixed]
+    python bench.py --workload triples      # nocc=32, nvir=480, naux=1600: one solve, (T) timed
 
 Prints one JSON line (rank 0). `value` is model TFLOP/s of whole solves with inputs resident in HBM
 (inputs of 0.5 GB exceed the 129 MB L2, so no flush is needed between steps); `e2e` repeats the
@@ -270,6 +271,9 @@ def run_batch(args):
                    "workers": args.workers, "autotune": args.autotune},
         "solves_per_s": world * args.nfrag / sec, "converged": n_ok, "n_frag": args.nfrag,
         "mean_ccsd_iterations": float(np.mean([r.n_iter for r in res])),
+        "not_converged": [{"frag": k, "status": r.status, "n_iter": r.n_iter,
+                           "shape": list(synth.batch_shapes(args.nfrag, seed)[k])}
+                          for k, r in enumerate(res) if r.status != lnocc.LNOCC_OK],
         "pipeline_occupancy": busy / sec,
         "input_generation_s": t_gen,
         "e2e": None, "e2e_note": "not measured for the batch workload (88 GB of inputs)",
@@ -278,6 +282,51 @@ def run_batch(args):
                      "kernel": "whole batch (model flops / wall time)",
                      "note": f"peak = {peak_src} bf16 burst {peak_burst} / 3 (BF16x3)"},
         "autotune_stats": lnocc.lnocc_autotune_stats(),
+        "clocks": sampler.summary(),
+    }), flush=True)
+
+
+def run_triples(args):
+    """(T)-dominated large fragment (nocc=32, nvir=480, naux=1600): one mixed solve, (T) timed."""
+    import torch
+    from paper_2407_11258_gb300 import build, lnocc, synth
+    world, rank, local = dist_setup()
+    build.build()
+    lnocc.load()
+    o, v, q = 32, 480, 1600
+    item = synth.fragment_device(o, v, q, False, 4000 + rank, "cuda", frag=(0,))
+    _, _, _, eps, B, U = item
+    stream = torch.cuda.current_stream()
+    opts = lnocc.default_opts(precision=lnocc.LNOCC_PREC_MIXED)
+    t0 = time.perf_counter()
+    f = lnocc.lnocc_build_ints(o, v, q, eps, B, opts)
+    t1 = time.perf_counter()
+    e, it, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
+    t2 = time.perf_counter()
+    sampler = ClockSampler(local)
+    with sampler:
+        et, etf = lnocc.lnocc_triples(f, U)
+    t3 = time.perf_counter()
+    info = f.info()
+    f.free()
+    _, trip = model_flops(o, v, 0)
+    alg = triples_algorithmic_flops(o, v)
+    peak_burst, peak_sust, hbm, peak_src = read_peaks()
+    achieved = alg / (info.t_triples_gemm_ms * 1e-3) / 1e12
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": trip / (info.t_triples_ms * 1e-3) / 1e12, "unit": "TFLOP/s ((T) model flops)",
+        "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": info.t_triples_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/fp32 (fp64 denominators and energy sum)",
+        "data": "synthetic", "config": {"workload": "(T)-dominated fragment nocc=32 nvir=480 naux=1600, 1 LMO"},
+        "energies": {"e_ccsd": e, "e_t": et, "e_t_frag": etf}, "ccsd_iterations": it,
+        "t_build_s": t1 - t0, "t_ccsd_s": t2 - t1, "t_triples_wall_s": t3 - t2,
+        "device_gb": info.device_bytes / 1e9,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_burst / 3.0, "unit": "TFLOP/s",
+                     "frac": achieved / (peak_burst / 3.0), "traffic": None,
+                     "kernel": "k_gemm_tc ((T) W contractions)", "contraction_ms": info.t_triples_gemm_ms,
+                     "note": f"useful 2o^3v^4+2o^4v^3 / contraction event time; peak = {peak_src} bf16 burst / 3"},
         "clocks": sampler.summary(),
     }), flush=True)
 
@@ -343,6 +392,18 @@ def run_mlp(args):
         t_mlp.append(c - b)
         de.append(abs(e1 - e0))
         f.free()
+    # the same comparison on the FP64 path, where converged energies can be compared at 1e-8 Eh
+    it0_64, it1_64, de_64 = [], [], []
+    for k in range(2000, 2000 + args.nheld_fp64):
+        o, v, q, eps, B, U = synth.mlp_fragment_device(k, dev)
+        f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=lnocc.LNOCC_PREC_FP64))
+        lnocc.lnocc_frag_set_mlp(f, m)
+        e0, n0, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
+        e1, n1, _ = lnocc.lnocc_ccsd(f, guess_mode=lnocc.LNOCC_GUESS_MLP, allow_noconv=True)
+        it0_64.append(n0)
+        it1_64.append(n1)
+        de_64.append(abs(e1 - e0))
+        f.free()
     if rank != 0:
         return
     print(json.dumps({
@@ -355,6 +416,9 @@ def run_mlp(args):
         "mean_iterations_mp2_guess": float(np.mean(it0)), "mean_iterations_mlp_guess": float(np.mean(it1)),
         "mean_ccsd_s_mp2_guess": float(np.mean(t_mp2)), "mean_ccsd_s_mlp_guess": float(np.mean(t_mlp)),
         "max_abs_dE_mlp_vs_mp2_guess": float(np.max(de)),
+        "fp64_path": {"n_frag": args.nheld_fp64, "mean_iterations_mp2_guess": float(np.mean(it0_64)) if it0_64 else None,
+                      "mean_iterations_mlp_guess": float(np.mean(it1_64)) if it1_64 else None,
+                      "max_abs_dE_mlp_vs_mp2_guess": float(np.max(de_64)) if de_64 else None},
         "train_loss_first": float(np.mean(losses[:10])), "train_loss_last": float(np.mean(losses[-50:])),
         "t_training_data_s": t_data, "t_training_s": t_train, "mean_iterations_training_solves": float(np.mean(it_train)),
     }), flush=True)
@@ -368,12 +432,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="diamond", choices=["diamond", "batch", "mlp"])
+    ap.add_argument("--workload", default="diamond", choices=["diamond", "batch", "mlp", "triples"])
     ap.add_argument("--ntrain", type=int, default=256, help="mlp workload: training solves")
     ap.add_argument("--nheld", type=int, default=64, help="mlp workload: held-out fragments")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--mlp-precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nheld-fp64", type=int, default=16, help="mlp workload: held-out fragments also run in FP64")
     ap.add_argument("--nfrag", type=int, default=128, help="batch workload: fragments per batch")
     ap.add_argument("--workers", type=int, default=0, help="batch workload: concurrent pipelines (0: library default)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1], help="batch workload: tile autotuning")
@@ -384,6 +449,8 @@ def main():
         return run_batch(args)
     if args.workload == "mlp":
         return run_mlp(args)
+    if args.workload == "triples":
+        return run_triples(args)
 
     import torch
     from paper_2407_11258_gb300 import build, lnocc, synth

@@ -235,7 +235,7 @@ int lnocc_solve_batch(int nfrag, const lnocc_batch_item* items, const lnocc_opts
 /*
  * Tile autotuner of the tensor-core GEMM (library-wide, all fragments; no counterpart in the paper).
  * The CTA tile width BN (32..256) of every tcgen05 contraction is picked per shape bucket
- * (M and K blocks in half-octaves, N in steps of 16, one or two K segments).
+ * (M and K blocks in octaves, N in half-octaves, one or two K segments).
  *   mode 0 (default): fixed rule (narrowest BN covering N);
  *   mode 1: table lookup, fixed rule on a miss;
  *   mode 2: like 1, but a miss first times every candidate on the call's own operands (into scratch,

@@ -214,6 +214,11 @@ __device__ __forceinline__ void red_add(float* p, float v) {
 __device__ __forceinline__ void red_add(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
+// four consecutive floats in one reduction (p 16-byte aligned): a quarter of the L2 atomic operations
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
 
 // Sixteen epilogue stores. beta = 1 accumulates with fire-and-forget reductions (each element is
 // touched once per launch, so launches on one stream still add in a fixed order); other beta values
@@ -581,6 +586,9 @@ __global__ void __launch_bounds__(256, 1)
     // ---------------- epilogue warps
     const int ew = warp - 4;  // TMEM lane quadrant
     const bool colmajor = !p.ws && (C.sn0 == 1 || C.sn0 == -1);
+    // FP32 accumulation into a destination with unit stride along columns or rows: 4-wide reductions
+    const bool vec_cols = !p.ws && C.dst32 && p.beta_f == 1.f && C.sn0 == 1;
+    const bool vec_rows = !p.ws && C.dst32 && p.beta_f == 1.f && !vec_cols && C.sm0 == 1;
     float* tile = epi + ew * (32 * 17);
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -594,7 +602,66 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const uint32_t acc = tmem + buf * Cfg::ACC_COLS + (static_cast<uint32_t>(ew * 32) << 16);
       const int M = ti.M;
-      if (p.ws) {  // split-K partials, FP64 row-major [z][M][N]
+      if (vec_cols || vec_rows) {
+        // The 32 x 16 block of each chunk goes through shared memory; a thread then owns either
+        // 4 rows x 4 consecutive columns (unit column stride) or 4 quads of 4 consecutive rows at one
+        // column (unit row stride), and adds each 4-vector with one red.v4 when the 4 destinations are
+        // consecutive and 16-byte aligned (scalar reductions otherwise).
+        const int m_lane = ti.m0 + ew * 32 + lane;
+        const long long rowoff = m_lane < ti.M ? ti.cbase + out_moff(C, m_lane) : -1;
+        const float al = p.alpha_f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(acc + c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tile[lane * 17 + j] = v[j];
+          __syncwarp();
+          if (vec_cols) {
+            const int q = lane & 3, rr = lane >> 2;
+            const int n = ti.n0 + c0 + 4 * q;
+            const long long no = n < p.N ? out_noff(C, n) : 0;
+            const bool quad = n + 3 < p.N && (n % C.ndiv) + 3 < C.ndiv;
+#pragma unroll
+            for (int t4 = 0; t4 < 4; ++t4) {
+              const int r = rr + 8 * t4;
+              const long long ro = __shfl_sync(0xffffffffu, rowoff, r);
+              if (ro < 0 || n >= p.N) continue;
+              float* dst = C.dst32 + ro + no;
+              const float* x = tile + r * 17 + 4 * q;
+              if (quad && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                red_add4(dst, al * x[0], al * x[1], al * x[2], al * x[3]);
+              } else {
+                for (int k = 0; k < 4 && n + k < p.N; ++k)
+                  red_add(C.dst32 + ro + out_noff(C, n + k), al * x[k]);
+              }
+            }
+          } else {
+            const int cc = lane & 15, g = lane >> 4;
+            const int n = ti.n0 + c0 + cc;
+            const long long no = n < p.N ? out_noff(C, n) : 0;
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const int r0 = 4 * (g + 2 * k4);
+              long long ro[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) ro[k] = __shfl_sync(0xffffffffu, rowoff, r0 + k);
+              if (n >= p.N) continue;
+              const float* x = tile + r0 * 17 + cc;
+              float* dst = C.dst32 + ro[0] + no;
+              if (ro[0] >= 0 && ro[3] == ro[0] + 3 && ro[1] == ro[0] + 1 && ro[2] == ro[0] + 2 &&
+                  (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                red_add4(dst, al * x[0], al * x[17], al * x[34], al * x[51]);
+              } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  if (ro[k] >= 0) red_add(C.dst32 + ro[k] + no, al * x[17 * k]);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      } else if (p.ws) {  // split-K partials, FP64 row-major [z][M][N]
         const int m = ti.m0 + ew * 32 + lane;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -789,8 +856,8 @@ static void launch_bn(int bn, const Packed& A0, const Packed& B0, const Packed* 
 // The N-width of the CTA tile (BN) decides the number of tiles (wave quantisation over the SMs), how
 // often each A tile is re-read, the TMEM columns and the pipeline depth. The fixed rule above takes
 // the narrowest BN that covers N; the tuner instead times every candidate on the real operands and
-// keeps the fastest per shape bucket (M and the K-block count in half-octaves, N in steps of 16,
-// one or two K segments). Timed runs write to a scratch copy of the output footprint with beta = 0,
+// keeps the fastest per shape bucket (M and the K-block count in octaves, N in half-octaves, one or
+// two K segments). Timed runs write to a scratch copy of the output footprint with beta = 0,
 // so the call's real output is written once, by the chosen configuration, afterwards. Batched
 // (per-entry table) launches always use the fixed rule.
 namespace {
@@ -810,8 +877,9 @@ Tuner& tuner() {
   static Tuner t;
   return t;
 }
+int octave(long long x) { return static_cast<int>(std::floor(std::log2(static_cast<double>(std::max(x, 1LL))))); }
 int half_octave(long long x) { return static_cast<int>(std::floor(2.0 * std::log2(static_cast<double>(std::max(x, 1LL))))); }
-TuneKey make_key(bool seg2, int M, int N, int nkb) { return TuneKey{seg2 ? 2 : 1, half_octave(M), (N + 15) / 16, half_octave(nkb)}; }
+TuneKey make_key(bool seg2, int M, int N, int nkb) { return TuneKey{seg2 ? 2 : 1, octave(M), half_octave(N), octave(nkb)}; }
 
 // element range [lo, hi] that an OutMap touches for m < M, n < N (host mirror of out_moff / out_noff)
 void out_extent(const OutMap& C, int M, int N, long long* lo, long long* hi) {

@@ -135,7 +135,9 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
 // s = 1/sqrt(-Delta) and -Delta = d_i + d_j + d_k, d_m = (e_a + e_b + e_c)/3 - e_m > 0 evaluated in FP64
 // (a sum of positive terms: no cancellation when it is rounded to Real). Threads then run over (j, k)
 // and every distinct ordering of (a, b, c); the i-sums are accumulated in Real and the block sum in FP64.
-template <typename TW, typename Real, int NLO>
+// VFLY: only w is staged and v = w + disc s is recomputed where it is read (the slices, t1 columns and
+// d_m are in shared memory already); half the shared memory, for blocks too large to stage both.
+template <typename TW, typename Real, int NLO, bool VFLY>
 __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
                                   const double* __restrict__ eps, const double* __restrict__ t1,
                                   const double* __restrict__ ovov, const double* __restrict__ U, int nlo_rt,
@@ -155,7 +157,7 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   Real* sw = reinterpret_cast<Real*>(smraw);
   Real* sv = sw + blk;
   const int P1 = o + 1, o2p = o * P1;  // o x o slices padded to odd row stride
-  Real* Sab = sv + blk;     // (y0 a|y1 b)
+  Real* Sab = VFLY ? sv : sv + blk;  // (y0 a|y1 b)
   Real* Sac = Sab + o2p;    // (y0 a|y2 c)
   Real* Sbc = Sac + o2p;    // (y1 b|y2 c)
   Real* ta = Sbc + o2p;     // t1[y][a], t1[y][b], t1[y][c]
@@ -193,7 +195,7 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
       sc = static_cast<Real>(1.0 / sqrt(static_cast<double>(d)));
     const int sidx = y0 * S0 + y1 * S1 + y2;
     sw[sidx] = Wv * sc;
-    sv[sidx] = (Wv + disc) * sc;
+    if (!VFLY) sv[sidx] = (Wv + disc) * sc;
   }
   __syncthreads();
   // the six slot permutations; with the loop fully unrolled every index below is a compile-time choice
@@ -223,7 +225,27 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
       for (int al = 0; al < NLO; ++al) zu[al] = yu[al] = 0;
       for (int i = 0; i < o; ++i) {
         const Real z = 4 * sw[base0 + i * si0] + sw[base1 + i * si1] + sw[base2 + i * si2];
-        const Real y = sv[base0 + i * si0] - sv[base3 + i * si3];
+        Real y;
+        if (!VFLY) {
+          y = sv[base0 + i * si0] - sv[base3 + i * si3];
+        } else {
+          // v = w + disc s at T = (slot p0 <- i, p1 <- j, p2 <- k) and at the reversed (p2 <- i, p0 <- k)
+          auto vdisc = [&](int y0, int y1, int y2) {
+            const Real dd = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
+            const Real d = dm[y0] + dm[y1] + dm[y2];
+            Real sc;
+            if (sizeof(Real) == 4)
+              sc = static_cast<Real>(rsqrtf(static_cast<float>(d)));
+            else
+              sc = static_cast<Real>(1.0 / sqrt(static_cast<double>(d)));
+            return dd * sc;
+          };
+          const int yt0 = p0 == 0 ? i : (p1 == 0 ? j : k), yt1 = p0 == 1 ? i : (p1 == 1 ? j : k),
+                    yt2 = p0 == 2 ? i : (p1 == 2 ? j : k);
+          const int yr0 = p2 == 0 ? i : (p1 == 0 ? j : k), yr1 = p2 == 1 ? i : (p1 == 1 ? j : k),
+                    yr2 = p2 == 2 ? i : (p1 == 2 ? j : k);
+          y = (sw[base0 + i * si0] + vdisc(yt0, yt1, yt2)) - (sw[base3 + i * si3] + vdisc(yr0, yr1, yr2));
+        }
         acc += z * y;
 #pragma unroll
         for (int al = 0; al < NLO; ++al) {
@@ -439,9 +461,11 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
 
   const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
-  const bool staged = 2LL * sblk * wsz + (3LL * o * (o + 1) + 4LL * o + 8LL * o) * wsz <= 200LL * 1024 && nlo <= 8;
+  const long long small_smem = (3LL * o * (o + 1) + 4LL * o + 8LL * o) * wsz;
+  const bool staged_full = 2LL * sblk * wsz + small_smem <= 200LL * 1024;
+  const bool staged = (staged_full || sblk * wsz + small_smem <= 200LL * 1024) && nlo <= 8;
   // (the staged kernel reads U padded to its compile-time LO count)
-  const size_t esmem = 2 * sblk * wsz + (3 * static_cast<size_t>(o) * (o + 1) + 4 * o + static_cast<size_t>(o) * 8) * wsz;
+  const size_t esmem = (staged_full ? 2 : 1) * sblk * wsz + static_cast<size_t>(small_smem);
   // the energy kernel is compiled for 0, 1, 2, 4 or 8 LOs; U is zero-padded to the next size
   const int nlo_t = nlo == 0 ? 0 : nlo <= 1 ? 1 : nlo <= 2 ? 2 : nlo <= 4 ? 4 : 8;
   double* dUp = nullptr;
@@ -458,9 +482,15 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   auto energy_launch = [&](const void* Wp, long long Sc, int b, int c0, int na, int nc, double* part) {
     dim3 grid(na, nc);
     count_launch();
-#define LN_E(T, R, K)                                                                                             \
-  k_t_energy_staged<T, R, K><<<grid, 256, esmem, s>>>(static_cast<const T*>(Wp), Sc, b, c0, o, v, eps, t1, ovov, \
-                                                      dUp, nlo_t, part)
+#define LN_E(T, R, K)                                                                                    \
+  do {                                                                                                   \
+    if (staged_full)                                                                                     \
+      k_t_energy_staged<T, R, K, false><<<grid, 256, esmem, s>>>(static_cast<const T*>(Wp), Sc, b, c0, o, v, \
+                                                                 eps, t1, ovov, dUp, nlo_t, part);       \
+    else                                                                                                 \
+      k_t_energy_staged<T, R, K, true><<<grid, 256, esmem, s>>>(static_cast<const T*>(Wp), Sc, b, c0, o, v,  \
+                                                                eps, t1, ovov, dUp, nlo_t, part);        \
+  } while (0)
     if (bf) {
       switch (nlo_t) {
         case 0: LN_E(float, float, 0); break;
@@ -489,16 +519,26 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       auto attr = [](const void* fn) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       };
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 0>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 1>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 2>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 4>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 8>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 4>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 8>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 0, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 1, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 2, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 4, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 8, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 4, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 8, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 0, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 1, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 2, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 4, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 8, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 4, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 8, true>));
     });
   } else if (bf) {
     cleanup();
@@ -560,12 +600,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       m.sn1 = o; m.sn0 = 1; m.ndiv = o;
       gemm2_batched(X1, TvT, &T2x, &O1T, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
     }
-    // sigma5 (batched over c): rows (a,k), cols (j,i): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
+    // sigma5 (batched over c): rows (a,k), cols (i,j): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
+    // (TvT[b][i][j][d] = t_ji^bd and O1T[b][i][j][l] = (bj|il): j runs fastest in the columns)
     {
       OutMap m = omap(1.0);
       m.sm1 = ooo; m.sm0 = o; m.mdiv = o;
-      m.sn1 = 1; m.sn0 = oo; m.ndiv = o;
-      gemm2_batched(X2, Tv, &T2y, &O1, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
+      m.sn1 = oo; m.sn0 = 1; m.ndiv = o;
+      gemm2_batched(X2, TvT, &T2y, &O1T, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
     }
     cudaEventRecord(e1, s);
     gev.emplace_back(e0, e1);

@@ -1,6 +1,6 @@
 """Run one fragment solve through the C-ABI (for profiling with external tools such as ncu).
 
-    python -m paper_2407_11258_gb300.profile_case --nocc 16 --nvir 120 --naux 480 --iters 4
+    python -m paper_2407_11258_gb300.profile_case --nocc 16 --nvir 120 --naux 480 --iters 4 [--mlp-guess]
 
 Builds the integrals, runs `--iters` CCSD iterations (mixed precision unless --fp64), the fragment
 energies and the (T) energy on a seeded synthetic fragment, and prints the timings the library reports.
@@ -19,6 +19,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--no-triples", action="store_true")
+    ap.add_argument("--mlp-guess", action="store_true", help="also run the learned-guess kernel once (initial weights)")
     a = ap.parse_args(argv)
     import torch
 
@@ -35,6 +36,15 @@ def main(argv=None):
     t1 = time.perf_counter()
     ec, em = lnocc.lnocc_fragment_energy(f, U)
     out = f"ccsd {it} iterations {1e3 * (t1 - t0):.1f} ms E={e:.12f} E_frag={ec:.12f}"
+    if a.mlp_guess:
+        m = lnocc.Mlp(synth.mlp_init())
+        t2g = torch.empty(a.nocc, a.nocc, a.nvir, a.nvir, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        tg = time.perf_counter()
+        lnocc.lnocc_mlp_guess(f, m, t2g)
+        torch.cuda.synchronize()
+        out += f"; learned guess {1e3 * (time.perf_counter() - tg):.2f} ms"
+        m.free()
     if not a.no_triples:
         et, etf = lnocc.lnocc_triples(f, U)
         inf = f.info()

@@ -202,3 +202,13 @@ def test_fault_paths(lnocc):
     with pytest.raises(lnocc.LnoccError) as ei:
         lnocc.lnocc_build_ints(3, 20, 80, bad, B, lnocc.default_opts())
     assert ei.value.code == lnocc.LNOCC_ENUMERIC
+
+
+@pytest.mark.parametrize("prec,o,tol", [(1, 30, MIXED_TOL), (0, 24, FP64_TOL)])
+def test_large_nocc_triples_w_only_staging(lnocc, prec, o, tol):
+    """nocc large enough that the (T) energy block stages only w and forms v where it is read
+    (FP32: nocc >= 29, FP64: nocc >= 23); small nvir keeps the oracle fast."""
+    fr = synth.make_fragment(o, 10, 60, 700 + o, decay=20.0, frag=(0, 1))
+    ref = oracle_solve(fr)
+    got = gpu_solve(lnocc, fr, prec)
+    assert_parity(got, ref, tol)
