@@ -66,22 +66,23 @@ __device__ __forceinline__ void put(void* out, long long idx, long long plane, d
 }
 
 // Row-major pack (K index contiguous or nearly so in the source): one warp per (row, 256-wide K chunk).
-// Writes rows [0, rows(v)) of a packed operand at `out` (plane stride `plane` elements).
+// Writes columns [0, Kw) of rows [0, rows(v)) at `out` (row stride ld, plane stride `plane` elements);
+// columns at or beyond K(v) are zero.
 template <bool BF16>
-__global__ void k_pack(View v, void* out, int Kp, long long plane) {
+__global__ void k_pack(View v, void* out, int Kw, int ld, long long plane) {
   const int K = v.K2 * v.K1 * v.K0;
   const int rows = v.R2 * v.R1 * v.R0;
   const int lane = threadIdx.x % 32;
   const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) / 32;
   const long long nwarp = static_cast<long long>(gridDim.x) * blockDim.x / 32;
-  const int nchunk = (Kp + 255) / 256;
+  const int nchunk = (Kw + 255) / 256;
   const long long items = static_cast<long long>(rows) * nchunk;
   const bool kflat = (v.K1 == 1 && v.K2 == 1);
   for (long long it = warp; it < items; it += nwarp) {
     const int r = static_cast<int>(it / nchunk), ch = static_cast<int>(it % nchunk);
     const double* src = v.src + view_roff(v, r);
-    const long long base = static_cast<long long>(r) * Kp;
-    const int kend = min(Kp, (ch + 1) * 256);
+    const long long base = static_cast<long long>(r) * ld;
+    const int kend = min(Kw, (ch + 1) * 256);
     for (int k = ch * 256 + lane; k < kend; k += 32) {
       double x = 0.0;
       if (k < K) x = v.scale * src[kflat ? static_cast<long long>(k) * v.sk0 : view_koff(v, k)];
@@ -93,7 +94,7 @@ __global__ void k_pack(View v, void* out, int Kp, long long plane) {
 // Transposing pack for sources whose rows are contiguous (sr0 == 1) and K is strided:
 // 32 x 32 tiles through shared memory so that both the reads and the writes are coalesced.
 template <bool BF16>
-__global__ void k_pack_t(View v, void* out, int Kp, long long plane) {
+__global__ void k_pack_t(View v, void* out, int Kw, int ld, long long plane) {
   __shared__ double tile[32][33];
   const int K = v.K2 * v.K1 * v.K0;
   const int rows = v.R2 * v.R1 * v.R0;
@@ -108,27 +109,27 @@ __global__ void k_pack_t(View v, void* out, int Kp, long long plane) {
   __syncthreads();
   for (int ry = ty; ry < 32; ry += 8) {
     const int r = rb + ry, k = kb + tx;
-    if (r < rows && k < Kp) put<BF16>(out, static_cast<long long>(r) * Kp + k, plane, tile[tx][ry]);
+    if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ry]);
   }
 }
 
-static void launch_pack(const View& v, void* out, int Kp, long long plane, bool bf16, cudaStream_t s) {
+static void launch_pack(const View& v, void* out, int Kw, int ld, long long plane, bool bf16, cudaStream_t s) {
   const int rows = v.rows();
   const bool transpose = v.sr0 == 1 && v.R0 >= 32 && (v.sk0 != 1);
   count_launch();
   if (transpose) {
-    dim3 grid((rows + 31) / 32, (Kp + 31) / 32);
+    dim3 grid((rows + 31) / 32, (Kw + 31) / 32);
     if (bf16)
-      k_pack_t<true><<<grid, 256, 0, s>>>(v, out, Kp, plane);
+      k_pack_t<true><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
     else
-      k_pack_t<false><<<grid, 256, 0, s>>>(v, out, Kp, plane);
+      k_pack_t<false><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
   } else {
-    const long long items = static_cast<long long>(rows) * ((Kp + 255) / 256);
+    const long long items = static_cast<long long>(rows) * ((Kw + 255) / 256);
     const int blocks = static_cast<int>(std::min<long long>((items + 7) / 8, 152LL * 32));
     if (bf16)
-      k_pack<true><<<std::max(blocks, 1), 256, 0, s>>>(v, out, Kp, plane);
+      k_pack<true><<<std::max(blocks, 1), 256, 0, s>>>(v, out, Kw, ld, plane);
     else
-      k_pack<false><<<std::max(blocks, 1), 256, 0, s>>>(v, out, Kp, plane);
+      k_pack<false><<<std::max(blocks, 1), 256, 0, s>>>(v, out, Kw, ld, plane);
   }
 }
 
@@ -136,16 +137,22 @@ void pack(const View& v, Packed& out, cudaStream_t s) {
   out.rows = v.rows();
   out.Kp = round_up(std::max(v.K(), 1), 64);
   const long long total = static_cast<long long>(out.rows) * out.Kp;
-  launch_pack(v, out.p, out.Kp, total, out.bf16, s);
+  launch_pack(v, out.p, out.Kp, out.Kp, total, out.bf16, s);
 }
 
 // Pack a view into rows [row0, row0 + v.rows()) of an existing packed operand `full`.
 void pack_rows(const View& v, Packed& full, int row0, cudaStream_t s) {
+  pack_cols(v, full, row0, 0, full.Kp, s);
+}
+
+// Pack a view into rows [row0, row0 + v.rows()) and columns [col0, col0 + width) of `full` (columns
+// at or beyond the view's K are written as zeros): lets two operands share one K dimension.
+void pack_cols(const View& v, Packed& full, int row0, int col0, int width, cudaStream_t s) {
   const long long plane = static_cast<long long>(full.rows) * full.Kp;
-  const size_t off = static_cast<size_t>(row0) * full.Kp;
+  const size_t off = static_cast<size_t>(row0) * full.Kp + col0;
   void* base = full.bf16 ? static_cast<void*>(static_cast<__nv_bfloat16*>(full.p) + off)
                          : static_cast<void*>(static_cast<double*>(full.p) + off);
-  launch_pack(v, base, full.Kp, plane, full.bf16, s);
+  launch_pack(v, base, width, full.Kp, plane, full.bf16, s);
 }
 
 __global__ void k_permute(View v, double* dst, double beta) {

@@ -79,6 +79,7 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // ---- kernels (launch wrappers); all enqueue on `s` and do not synchronize
 void pack(const View& v, Packed& out, cudaStream_t s);
 void pack_rows(const View& v, Packed& full, int row0, cudaStream_t s);
+void pack_cols(const View& v, Packed& full, int row0, int col0, int width, cudaStream_t s);
 // dst[r*K + k] = view(r, k) + beta * dst[r*K + k]   (FP64, no padding)
 void permute(const View& v, double* dst, double beta, cudaStream_t s);
 void gemm_f64(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s);

@@ -198,65 +198,83 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
     if (!VFLY) sv[sidx] = (Wv + disc) * sc;
   }
   __syncthreads();
-  // the six slot permutations; with the loop fully unrolled every index below is a compile-time choice
+  // The six placements of (i, j, k) into the slots of W^{abc}_y: placement q puts i in slot PM[q][0],
+  // j in PM[q][1], k in PM[q][2]. For ordering (p0, p1, p2) of the virtual labels, the four W values it
+  // needs -- T, T o c, T o c^2 and the reversal -- are the placements (p0,p1,p2), (p1,p2,p0), (p2,p0,p1)
+  // and (p2,p1,p0). Each thread loads the six w (and v) placements once per i and evaluates every
+  // distinct ordering from registers. With the loops fully unrolled every index is a compile-time choice.
   constexpr int PM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   const int x0 = a, x1 = b, x2 = c;
+  auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
+  auto SS = [&](int p) { return p == 0 ? S0 : (p == 1 ? S1 : 1); };
+  bool act[6];  // orderings with distinct label sequences (equal labels repeat an ordering)
+#pragma unroll
+  for (int pi = 0; pi < 6; ++pi) {
+    bool dup = false;
+#pragma unroll
+    for (int q = 0; q < pi; ++q)
+      dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
+    act[pi] = !dup;
+  }
   Real r_can = 0, r_frag = 0;  // per-thread partials (converted to FP64 for the block sum)
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
+    int off[6], si[6];
 #pragma unroll
-    for (int pi = 0; pi < 6; ++pi) {
-      const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
-      auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
-      auto SS = [&](int p) { return p == 0 ? S0 : (p == 1 ? S1 : 1); };
-      bool dup = false;
+    for (int q = 0; q < 6; ++q) {
+      off[q] = j * SS(PM[q][1]) + k * SS(PM[q][2]);
+      si[q] = SS(PM[q][0]);
+    }
+    Real acc = 0, zu[6][NLO > 0 ? NLO : 1], yu[6][NLO > 0 ? NLO : 1];
 #pragma unroll
-      for (int q = 0; q < pi; ++q)
-        dup = dup || (X(PM[q][0]) == X(p0) && X(PM[q][1]) == X(p1) && X(PM[q][2]) == X(p2));
-      if (dup) continue;
-      // offsets of W^{abc}_y for the four orderings: T (p0,p1,p2), T o c (p1,p2,p0), T o c^2 (p2,p0,p1),
-      // reversed (p2,p1,p0); slot p receives i, j or k.
-      const int base0 = j * SS(p1) + k * SS(p2), si0 = SS(p0);
-      const int base1 = j * SS(p2) + k * SS(p0), si1 = SS(p1);
-      const int base2 = j * SS(p0) + k * SS(p1), si2 = SS(p2);
-      const int base3 = j * SS(p1) + k * SS(p0), si3 = SS(p2);
-      Real acc = 0, zu[NLO > 0 ? NLO : 1], yu[NLO > 0 ? NLO : 1];
+    for (int pi = 0; pi < 6; ++pi)
 #pragma unroll
-      for (int al = 0; al < NLO; ++al) zu[al] = yu[al] = 0;
-      for (int i = 0; i < o; ++i) {
-        const Real z = 4 * sw[base0 + i * si0] + sw[base1 + i * si1] + sw[base2 + i * si2];
-        Real y;
+      for (int al = 0; al < NLO; ++al) zu[pi][al] = yu[pi][al] = 0;
+    for (int i = 0; i < o; ++i) {
+      Real wq[6], vq[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        wq[q] = sw[off[q]];
         if (!VFLY) {
-          y = sv[base0 + i * si0] - sv[base3 + i * si3];
+          vq[q] = sv[off[q]];
         } else {
-          // v = w + disc s at T = (slot p0 <- i, p1 <- j, p2 <- k) and at the reversed (p2 <- i, p0 <- k)
-          auto vdisc = [&](int y0, int y1, int y2) {
-            const Real dd = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
-            const Real d = dm[y0] + dm[y1] + dm[y2];
-            Real sc;
-            if (sizeof(Real) == 4)
-              sc = static_cast<Real>(rsqrtf(static_cast<float>(d)));
-            else
-              sc = static_cast<Real>(1.0 / sqrt(static_cast<double>(d)));
-            return dd * sc;
-          };
-          const int yt0 = p0 == 0 ? i : (p1 == 0 ? j : k), yt1 = p0 == 1 ? i : (p1 == 1 ? j : k),
-                    yt2 = p0 == 2 ? i : (p1 == 2 ? j : k);
-          const int yr0 = p2 == 0 ? i : (p1 == 0 ? j : k), yr1 = p2 == 1 ? i : (p1 == 1 ? j : k),
-                    yr2 = p2 == 2 ? i : (p1 == 2 ? j : k);
-          y = (sw[base0 + i * si0] + vdisc(yt0, yt1, yt2)) - (sw[base3 + i * si3] + vdisc(yr0, yr1, yr2));
+          // v = w + disc s at this placement (slices, t1 columns and d_m are staged)
+          const int y0 = PM[q][0] == 0 ? i : (PM[q][1] == 0 ? j : k);
+          const int y1 = PM[q][0] == 1 ? i : (PM[q][1] == 1 ? j : k);
+          const int y2 = PM[q][0] == 2 ? i : (PM[q][1] == 2 ? j : k);
+          const Real dd = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
+          const Real d = dm[y0] + dm[y1] + dm[y2];
+          Real sc;
+          if (sizeof(Real) == 4)
+            sc = static_cast<Real>(rsqrtf(static_cast<float>(d)));
+          else
+            sc = static_cast<Real>(1.0 / sqrt(static_cast<double>(d)));
+          vq[q] = wq[q] + dd * sc;
         }
+        off[q] += si[q];
+      }
+#pragma unroll
+      for (int pi = 0; pi < 6; ++pi) {
+        if (!act[pi]) continue;
+        const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
+        auto idx = [&](int s0, int s1) {  // placement index of the tuple (s0, s1, 3 - s0 - s1)
+          return s0 == 0 ? (s1 == 1 ? 0 : 1) : (s0 == 1 ? (s1 == 0 ? 2 : 3) : (s1 == 0 ? 4 : 5));
+        };
+        const Real z = 4 * wq[idx(p0, p1)] + wq[idx(p1, p2)] + wq[idx(p2, p0)];
+        const Real y = vq[idx(p0, p1)] - vq[idx(p2, p1)];
         acc += z * y;
 #pragma unroll
         for (int al = 0; al < NLO; ++al) {
-          zu[al] += Us[i * NLO + al] * z;
-          yu[al] += Us[i * NLO + al] * y;
+          zu[pi][al] += Us[i * NLO + al] * z;
+          yu[pi][al] += Us[i * NLO + al] * y;
         }
       }
-      r_can += acc;
-#pragma unroll
-      for (int al = 0; al < NLO; ++al) r_frag += zu[al] * yu[al];
     }
+    r_can += acc;
+#pragma unroll
+    for (int pi = 0; pi < 6; ++pi)
+#pragma unroll
+      for (int al = 0; al < NLO; ++al) r_frag += zu[pi][al] * yu[pi][al];
   }
   double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
   __shared__ double sh[2][32];
@@ -360,29 +378,31 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     if (P.p) cudaMemsetAsync(P.p, 0, static_cast<size_t>(rows) * P.Kp * (bf ? 4 : 8), s);
     return P;
   };
-  Packed X1 = mk(static_cast<int>(vv * o), v), X2 = mk(static_cast<int>(vv * o), v);
-  Packed Tv = mk(static_cast<int>(v * oo), v), TvT = mk(static_cast<int>(v * oo), v);
-  Packed T2x = mk(static_cast<int>(vv * o), o), T2y = mk(static_cast<int>(vv * o), o);
-  Packed O1 = mk(static_cast<int>(v * oo), o), O1T = mk(static_cast<int>(v * oo), o);
+  // Each (T) term is d-part (K = v) + l-part (K = o): the two operands of a side share one packed row
+  // space, so they are packed side by side along K (columns [0, v) and [v, v + o)) and every term is a
+  // single contraction of length v + o (no second, mostly padded, K segment).
+  //   XT1[x][a][i] = [ (ai|xd) | -t_il^ax ],   XT2[c][a][k] = [ (kc|ad) | -t_kl^ca ]
+  //   TO[z][r][q]  = [ t_rq^zd | (zr|ql) ],     TOT[z][k][j] = [ t_jk^zd | (zj|kl) ]
+  const int Kt = v + o;
+  Packed XT1 = mk(static_cast<int>(vv * o), Kt), XT2 = mk(static_cast<int>(vv * o), Kt);
+  Packed TO = mk(static_cast<int>(v * oo), Kt), TOT = mk(static_cast<int>(v * oo), Kt);
   double* ovoo = static_cast<double*>(tmp_alloc(ooo * v * 8));
   const double* dU = nlo > 0 ? U : nullptr;
-  if (!X1.p || !X2.p || !Tv.p || !TvT.p || !T2x.p || !T2y.p || !O1.p || !O1T.p || !ovoo) {
+  if (!XT1.p || !XT2.p || !TO.p || !TOT.p || !ovoo) {
     cleanup();
     set_error("lnocc_triples: device allocation failed (operands)");
     return LNOCC_ENOMEM;
   }
-  // amplitudes: Tv[z][r][q][d] = t_rq^zd, TvT[z][k][j][d] = t_jk^zd,
-  // T2x[x][a][i][l] = -t_il^ax, T2y[c][a][k][l] = -t_kl^ca (the l-terms enter W with a minus sign)
-  pack(view(t2, A_(v, v), A_(o, o * vv), A_(o, vv), kOne, kOne, A_(v, 1)), Tv, s);
-  pack(view(t2, A_(v, v), A_(o, vv), A_(o, o * vv), kOne, kOne, A_(v, 1)), TvT, s);
-  pack(view(t2, A_(v, 1), A_(v, v), A_(o, o * vv), kOne, kOne, A_(o, vv), -1.0), T2x, s);
-  pack(view(t2, A_(v, v), A_(v, 1), A_(o, o * vv), kOne, kOne, A_(o, vv), -1.0), T2y, s);
-  // (kz|jl) -> O1[z][k][j][l] = (zk|jl), O1T[z][k][j][l] = (zj|kl)
+  const int wl = XT1.Kp - v;  // width of the l-part columns, zero padding included
+  // amplitudes: TO[z][r][q][d] = t_rq^zd, TOT[z][k][j][d] = t_jk^zd (columns [0, v))
+  pack_cols(view(t2, A_(v, v), A_(o, o * vv), A_(o, vv), kOne, kOne, A_(v, 1)), TO, 0, 0, v, s);
+  pack_cols(view(t2, A_(v, v), A_(o, vv), A_(o, o * vv), kOne, kOne, A_(v, 1)), TOT, 0, 0, v, s);
+  // (kz|jl) -> TO[z][k][j][v + l] = (zk|jl), TOT[z][k][j][v + l] = (zj|kl)
   contract(view(Bov, kOne, kOne, A_(static_cast<int>(ov), 1), kOne, kOne, A_(N, ov)),
            view(Boo, kOne, kOne, A_(static_cast<int>(oo), 1), kOne, kOne, A_(N, oo)), out_rowmajor(ovoo, oo), true);
-  pack(view(ovoo, A_(v, oo), A_(o, v * oo), A_(o, o), kOne, kOne, A_(o, 1)), O1, s);
-  pack(view(ovoo, A_(v, oo), A_(o, o), A_(o, v * oo), kOne, kOne, A_(o, 1)), O1T, s);
-  // (jb|ad) -> X2[b][a][j][d], in chunks of b; X1[y][a][i][d] = (ai|yd) = X2[a][y][i][d]
+  pack_cols(view(ovoo, A_(v, oo), A_(o, v * oo), A_(o, o), kOne, kOne, A_(o, 1)), TO, 0, v, wl, s);
+  pack_cols(view(ovoo, A_(v, oo), A_(o, o), A_(o, v * oo), kOne, kOne, A_(o, 1)), TOT, 0, v, wl, s);
+  // (jb|ad) -> XT2[b][a][j][d], in chunks of b; XT1[y][a][i][d] = (ai|yd) = XT2[a][y][i][d]
   {
     Packed PBvv = mk(static_cast<int>(vv), N);
     if (!PBvv.p) {
@@ -404,19 +424,23 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       const int nb = std::min(bc, v - b0);
       contract_packed_b(view(Bov + b0, kOne, A_(o, v), A_(nb, 1), kOne, kOne, A_(N, ov)), PBvv, static_cast<int>(vv),
                         out_rowmajor(tmp, vv));
-      pack_rows(view(tmp, A_(nb, vv), A_(v, v), A_(o, nb * vv), kOne, kOne, A_(v, 1)), X2, b0 * v * o, s);
+      pack_cols(view(tmp, A_(nb, vv), A_(v, v), A_(o, nb * vv), kOne, kOne, A_(v, 1)), XT2, b0 * v * o, 0, v, s);
     }
     mixed = keep;
-    const long long tot = static_cast<long long>(X2.rows) * X2.Kp * (bf ? 2 : 1);
+    const long long tot = static_cast<long long>(XT2.rows) * XT2.Kp * (bf ? 2 : 1);
     const int blocks = static_cast<int>(std::min<long long>((tot + 255) / 256, 152LL * 32));
     count_launch();
     if (bf)
-      k_swap_outer_rows<unsigned short><<<blocks, 256, 0, s>>>(static_cast<const unsigned short*>(X2.p),
-                                                                 static_cast<unsigned short*>(X1.p), v, o, X2.Kp, 2);
+      k_swap_outer_rows<unsigned short><<<blocks, 256, 0, s>>>(static_cast<const unsigned short*>(XT2.p),
+                                                                 static_cast<unsigned short*>(XT1.p), v, o, XT2.Kp, 2);
     else
-      k_swap_outer_rows<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(X2.p), static_cast<double*>(X1.p), v,
-                                                       o, X2.Kp, 1);
+      k_swap_outer_rows<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(XT2.p), static_cast<double*>(XT1.p),
+                                                       v, o, XT2.Kp, 1);
   }
+  // l-parts (after the row swap, which copies whole rows): XT1[x][a][i][v + l] = -t_il^ax,
+  // XT2[c][a][k][v + l] = -t_kl^ca (the l-terms enter W with a minus sign)
+  pack_cols(view(t2, A_(v, 1), A_(v, v), A_(o, o * vv), kOne, kOne, A_(o, vv), -1.0), XT1, 0, v, wl, s);
+  pack_cols(view(t2, A_(v, v), A_(v, 1), A_(o, o * vv), kOne, kOne, A_(o, vv), -1.0), XT2, 0, v, wl, s);
 
   // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
@@ -564,49 +588,49 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    // W layout [c - c0][a][i][k][j]; each term's d-part (K = v) and l-part (K = o) accumulate in TMEM.
+    // W layout [c - c0][a][i][k][j]; each term is one contraction over K = v + o (d-part, then l-part).
     // sigma1: rows (a,i), cols (c,k,j): (ai|bd) t_kj^cd - t_il^ab (ck|jl)   [first writer]
     {
       OutMap m = omap(0.0);
       m.sm1 = ooo; m.sm0 = oo; m.mdiv = o;
       m.sn2 = Sc; m.sn1 = o; m.sn0 = 1; m.ndiv = o; m.ndiv1 = o;
-      gemm2_off(X1, xb, Tv, c0 * o2, v, T2x, xb, O1, c0 * o2, o, Ma, nc * o2, m, s, dstatus);
+      gemm_off(XT1, xb, TO, c0 * o2, Ma, nc * o2, Kt, m, s, dstatus);
     }
     // sigma3: rows (a,j), cols (c,k,i): (bj|ad) t_ki^cd - t_jl^ba (ck|il)
     {
       OutMap m = omap(1.0);
       m.sm1 = ooo; m.sm0 = 1; m.mdiv = o;
       m.sn2 = Sc; m.sn1 = o; m.sn0 = oo; m.ndiv = o; m.ndiv1 = o;
-      gemm2_off(X2, xb, Tv, c0 * o2, v, T2y, xb, O1, c0 * o2, o, Ma, nc * o2, m, s, dstatus);
+      gemm_off(XT2, xb, TO, c0 * o2, Ma, nc * o2, Kt, m, s, dstatus);
     }
     // sigma4: rows (a,i,k), cols (c,j): t_ik^ad (bj|cd) - (ai|kl) t_jl^bc
     {
       OutMap m = omap(1.0);
       m.sm2 = ooo; m.sm1 = oo; m.sm0 = o; m.mdiv = o; m.mdiv1 = o;
       m.sn1 = Sc; m.sn0 = 1; m.ndiv = o;
-      gemm2_off(Tv, 0, X2, xb + c0 * o, v, O1, 0, T2y, xb + c0 * o, o, Ma2, nc * o, m, s, dstatus);
+      gemm_off(TO, 0, XT2, xb + c0 * o, Ma2, nc * o, Kt, m, s, dstatus);
     }
     // sigma6: rows (a,i,j), cols (c,k): t_ij^ad (ck|bd) - (ai|jl) t_kl^cb
     {
       OutMap m = omap(1.0);
       m.sm2 = ooo; m.sm1 = oo; m.sm0 = 1; m.mdiv = o; m.mdiv1 = o;
       m.sn1 = Sc; m.sn0 = o; m.ndiv = o;
-      gemm2_off(Tv, 0, X1, xb + c0 * o, v, O1, 0, T2x, xb + c0 * o, o, Ma2, nc * o, m, s, dstatus);
+      gemm_off(TO, 0, XT1, xb + c0 * o, Ma2, nc * o, Kt, m, s, dstatus);
     }
     // sigma2 (batched over c): rows (a,i), cols (k,j): (ai|cd) t_jk^bd - t_il^ac (bj|kl)
     {
       OutMap m = omap(1.0);
       m.sm1 = ooo; m.sm0 = oo; m.mdiv = o;
       m.sn1 = o; m.sn0 = 1; m.ndiv = o;
-      gemm2_batched(X1, TvT, &T2x, &O1T, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
+      gemm_batched(XT1, TOT, dbat + ch.tab, nc, Ma, o2, Kt, m, s, dstatus);
     }
     // sigma5 (batched over c): rows (a,k), cols (i,j): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
-    // (TvT[b][i][j][d] = t_ji^bd and O1T[b][i][j][l] = (bj|il): j runs fastest in the columns)
+    // (TOT[b][i][j] = [t_ji^bd | (bj|il)]: j runs fastest in the columns)
     {
       OutMap m = omap(1.0);
       m.sm1 = ooo; m.sm0 = o; m.mdiv = o;
       m.sn1 = oo; m.sn0 = 1; m.ndiv = o;
-      gemm2_batched(X2, TvT, &T2y, &O1T, dbat + ch.tab, nc, Ma, o2, v, o, m, s, dstatus);
+      gemm_batched(XT2, TOT, dbat + ch.tab, nc, Ma, o2, Kt, m, s, dstatus);
     }
     cudaEventRecord(e1, s);
     gev.emplace_back(e0, e1);
