@@ -252,6 +252,8 @@ def run_batch(args):
             st, res = lnocc.lnocc_solve_batch(items, opts, mk(2 if args.autotune else 0), stream=stream,
                                               allow_noconv=True)
             times.append(time.perf_counter() - t1)
+    if args.autotune and args.save_tune:
+        lnocc.lnocc_autotune_save(args.save_tune)
     barrier(world)
     sec = max_over_ranks(world, float(np.mean(times)))
     flops = sum(r.model_flops for r in res)
@@ -442,6 +444,8 @@ def main():
     ap.add_argument("--nfrag", type=int, default=128, help="batch workload: fragments per batch")
     ap.add_argument("--workers", type=int, default=0, help="batch workload: concurrent pipelines (0: library default)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1], help="batch workload: tile autotuning")
+    ap.add_argument("--tune", action="store_true", help="diamond workload: tile autotuning during warm-up")
+    ap.add_argument("--save-tune", default=None, help="write the tile table to this file after tuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -469,8 +473,12 @@ def main():
     stream.synchronize()
     opts = lnocc.default_opts(precision=lnocc.LNOCC_PREC_MIXED)
     fr_dev = (eps_d, B_d, U_d, o, v, q)
-    for _ in range(args.warmup):
+    for w in range(args.warmup):
+        if args.tune:  # the first warm-up solve times the tile candidates; later solves use the table
+            lnocc.lnocc_autotune(2 if w == 0 else 1)
         res = solve_once(lnocc, fr_dev, opts, stream)
+    if args.tune and args.save_tune:
+        lnocc.lnocc_autotune_save(args.save_tune)
     # ---- device-resident timed region
     barrier(world)
     torch.cuda.synchronize()
@@ -515,7 +523,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3/fp32 (fp64 update, DIIS, energies)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "inputs (0.5 GB B tensor) larger than L2; no flush",
-                   "ccsd_iterations": n_iter},
+                   "ccsd_iterations": n_iter, "tile_autotune": bool(args.tune)},
         "solves_per_s": world * 1e3 / ms,
         "energies": {k: runs[-1][k] for k in ("e_mp2", "e_ccsd", "e_ccsd_frag", "e_mp2_frag", "e_t", "e_t_frag")},
         "e2e": {"value": world * flops_solve / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
