@@ -80,7 +80,9 @@ long long estimate_fragment_bytes(int o_, int v_, int N_, bool mixed, int n_refi
     long long t = esz * (2 * vv * o * kp(v) + 2 * v * oo * kp(v) + 2 * vv * o * kp(o) + 2 * v * oo * kp(o) +
                          vv * kp(N));
     t += 8 * (oo * ov + std::max(1LL, std::min(v, (1LL << 26) / (o * vv))) * o * vv);
-    t += std::max(192LL << 20, esz * v * oo * o) + 16 * v * v * v;
+    long long max_slab = 0;
+    for (long long bb = 0; bb < v; ++bb) max_slab = std::max(max_slab, (bb + 1) * (v - bb) * oo * o);
+    t += std::max(std::min(768LL << 20, esz * max_slab), esz * v * oo * o) + 16 * v * v * v;
     b += t;
   }
   return b + b / 16 + (64LL << 20);

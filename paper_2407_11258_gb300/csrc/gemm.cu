@@ -413,7 +413,8 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int EPI_BYTES = 4 * 32 * 17 * 4;  // epilogue transpose scratch (4 warps)
+  // epilogue scratch: the transpose tiles of 4 warps, or per warp BN column offsets + BN/4 flags
+  static constexpr int EPI_BYTES = 4 * 32 * 17 * 4 > 4 * (BN * 8 + BN / 4) ? 4 * 32 * 17 * 4 : 4 * (BN * 8 + BN / 4);
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 4 ? 4 : (192 * 1024) / STAGE_BYTES;
   static constexpr int ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two accumulators: MMA of tile t+1 overlaps epilogue of t
@@ -593,9 +594,8 @@ __global__ void __launch_bounds__(256, 1)
     // ---------------- epilogue warps
     const int ew = warp - 4;  // TMEM lane quadrant
     const bool colmajor = !p.ws && (C.sn0 == 1 || C.sn0 == -1);
-    // FP32 accumulation into a destination with unit stride along columns or rows: 4-wide reductions
-    const bool vec_cols = !p.ws && C.dst32 && p.beta_f == 1.f && C.sn0 == 1;
-    const bool vec_rows = !p.ws && C.dst32 && p.beta_f == 1.f && !vec_cols && C.sm0 == 1;
+    // FP32 destination with beta 0 or 1: direct row writes with per-tile column offsets (below)
+    const bool f32_direct = !p.ws && C.dst32 && (p.beta_f == 1.f || p.beta_f == 0.f);
     float* tile = epi + ew * (32 * 17);
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -609,64 +609,62 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const uint32_t acc = tmem + buf * Cfg::ACC_COLS + (static_cast<uint32_t>(ew * 32) << 16);
       const int M = ti.M;
-      if (vec_cols || vec_rows) {
-        // The 32 x 16 block of each chunk goes through shared memory; a thread then owns either
-        // 4 rows x 4 consecutive columns (unit column stride) or 4 quads of 4 consecutive rows at one
-        // column (unit row stride), and adds each 4-vector with one red.v4 when the 4 destinations are
-        // consecutive and 16-byte aligned (scalar reductions otherwise).
-        const int m_lane = ti.m0 + ew * 32 + lane;
-        const long long rowoff = m_lane < ti.M ? ti.cbase + out_moff(C, m_lane) : -1;
+      if (f32_direct) {
+        // FP32 destination, beta 0 or 1 (the (T) W terms). Each epilogue warp computes the column
+        // offsets of the tile once into its own shared-memory slot, with a flag per group of 4 columns
+        // that are consecutive and 16-byte aligned in the destination (warp-local: no barrier across
+        // warps). Each thread then writes its own accumulator row straight from the TMEM load: one
+        // 4-wide store / reduction per flagged group, scalar otherwise (with unit row stride the lanes
+        // of a warp still cover consecutive addresses).
+        long long* colo = reinterpret_cast<long long*>(epi) + ew * BN;
+        uint8_t* qok = reinterpret_cast<uint8_t*>(reinterpret_cast<long long*>(epi) + 4 * BN) + ew * (BN / 4);
+        __syncwarp();  // the previous tile's offsets are no longer read
+        for (int q = lane; q < BN / 4; q += 32) {
+          long long co[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int n = ti.n0 + 4 * q + k;
+            co[k] = n < p.N ? out_noff(C, n) : -1;
+            colo[4 * q + k] = co[k];
+          }
+          qok[q] = co[0] >= 0 && co[3] >= 0 && co[1] == co[0] + 1 && co[2] == co[0] + 2 && co[3] == co[0] + 3 &&
+                   (co[0] & 3) == 0;
+        }
+        __syncwarp();
+        const int m = ti.m0 + ew * 32 + lane;
+        const bool mvalid = m < ti.M;
+        const long long rowoff = mvalid ? ti.cbase + out_moff(C, m) : 0;
+        float* rowp = C.dst32 + rowoff;
+        const bool rowv4 = mvalid && (reinterpret_cast<uintptr_t>(rowp) & 15) == 0;
         const float al = p.alpha_f;
+        const bool acc_mode = p.beta_f == 1.f;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
           float v[16];
           tmem_ld16(acc + c0, v);
+          if (!mvalid) continue;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) tile[lane * 17 + j] = v[j];
-          __syncwarp();
-          if (vec_cols) {
-            const int q = lane & 3, rr = lane >> 2;
-            const int n = ti.n0 + c0 + 4 * q;
-            const long long no = n < p.N ? out_noff(C, n) : 0;
-            const bool quad = n + 3 < p.N && (n % C.ndiv) + 3 < C.ndiv;
+          for (int g4 = 0; g4 < 4; ++g4) {
+            const int q = (c0 >> 2) + g4;
+            if (rowv4 && qok[q]) {
+              float* d = rowp + colo[4 * q];
+              const float a0 = al * v[4 * g4], a1 = al * v[4 * g4 + 1], a2 = al * v[4 * g4 + 2], a3 = al * v[4 * g4 + 3];
+              if (acc_mode)
+                red_add4(d, a0, a1, a2, a3);
+              else
+                *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+            } else {
 #pragma unroll
-            for (int t4 = 0; t4 < 4; ++t4) {
-              const int r = rr + 8 * t4;
-              const long long ro = __shfl_sync(0xffffffffu, rowoff, r);
-              if (ro < 0 || n >= p.N) continue;
-              float* dst = C.dst32 + ro + no;
-              const float* x = tile + r * 17 + 4 * q;
-              if (quad && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-                red_add4(dst, al * x[0], al * x[1], al * x[2], al * x[3]);
-              } else {
-                for (int k = 0; k < 4 && n + k < p.N; ++k)
-                  red_add(C.dst32 + ro + out_noff(C, n + k), al * x[k]);
-              }
-            }
-          } else {
-            const int cc = lane & 15, g = lane >> 4;
-            const int n = ti.n0 + c0 + cc;
-            const long long no = n < p.N ? out_noff(C, n) : 0;
-#pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const int r0 = 4 * (g + 2 * k4);
-              long long ro[4];
-#pragma unroll
-              for (int k = 0; k < 4; ++k) ro[k] = __shfl_sync(0xffffffffu, rowoff, r0 + k);
-              if (n >= p.N) continue;
-              const float* x = tile + r0 * 17 + cc;
-              float* dst = C.dst32 + ro[0] + no;
-              if (ro[0] >= 0 && ro[3] == ro[0] + 3 && ro[1] == ro[0] + 1 && ro[2] == ro[0] + 2 &&
-                  (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-                red_add4(dst, al * x[0], al * x[17], al * x[34], al * x[51]);
-              } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                  if (ro[k] >= 0) red_add(C.dst32 + ro[k] + no, al * x[17 * k]);
+              for (int k = 0; k < 4; ++k) {
+                const long long co = colo[4 * q + k];
+                if (co < 0) continue;
+                if (acc_mode)
+                  red_add(rowp + co, al * v[4 * g4 + k]);
+                else
+                  rowp[co] = al * v[4 * g4 + k];
               }
             }
           }
-          __syncwarp();
         }
       } else if (p.ws) {  // split-K partials, FP64 row-major [z][M][N]
         const int m = ti.m0 + ew * 32 + lane;

@@ -444,9 +444,14 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 
   // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
-  long long chunk_mb = 192;
+  // W chunk: up to 768 MB (fewer, larger contraction launches measured faster than chunks that fit
+  // L2), but never more than the largest slab (b + 1)(v - b) o^3 needs
+  long long chunk_mb = 768;
   if (const char* e = std::getenv("LNOCC_TCHUNK_MB")) chunk_mb = std::max(1, std::atoi(e));
-  const long long welems = std::max<long long>((chunk_mb << 20) / static_cast<long long>(wsz), v * ooo);
+  long long max_slab = 0;
+  for (int bb = 0; bb < v; ++bb) max_slab = std::max(max_slab, 1LL * (bb + 1) * (v - bb) * ooo);
+  const long long welems = std::max<long long>(
+      std::min<long long>((chunk_mb << 20) / static_cast<long long>(wsz), max_slab), v * ooo);
   void* W = tmp_alloc(static_cast<size_t>(welems) * wsz);
   long long nblk_total = 0;
   for (int b = 0; b < v; ++b) nblk_total += 1LL * (b + 1) * (v - b);
