@@ -270,8 +270,18 @@ int Frag::build(const double* eps_in, const double* B_in) {
   }
 
   // ---- (ia|jb) = sum_Q B_Qia B_Qjb  (FP64 always: it feeds the energies)
-  contract(view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)),
-           view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov)), out_rowmajor(ovov, ov), true);
+  {  // symmetric in (ia) <-> (jb): the FP64 product computes one triangle of tiles and mirrors it
+    Packed PA;
+    PA.p = scrA;
+    PA.bf16 = false;
+    const View vb = view(Bov, kOne, kOne, A(static_cast<int>(ov), 1), kOne, kOne, A(N, ov));
+    if (static_cast<size_t>(vb.rows()) * round_up(std::max(vb.K(), 1), 64) * 8 > scr_bytes) {
+      scratch_overflow = true;
+    } else {
+      pack(vb, PA, s);
+      gemm_f64_sym(PA, static_cast<int>(ov), out_rowmajor(ovov, ov), s);
+    }
+  }
   launch_pair_L(ovov, Lpair, o, v, s);
   launch_mp2_amps(ovov, eps, t2mp2, o, v, s);
 

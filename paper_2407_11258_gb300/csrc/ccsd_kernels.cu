@@ -327,19 +327,42 @@ __global__ void k_pair_L(const double* ovov, double* L, int o, int v) {
 
 // V+/-[ab][cd] from G[a][c][b][d] = (ac|bd) for rows with a in [a0, a0 + na):
 //   V+ = (ac|bd) + (ad|bc) (a<=b, c<=d),  V- = (ac|bd) - (ad|bc) (a<b, c<d)
+// V+-[ab][cd] from G[al][c][b][d] = (a0+al c|b d): for fixed (al, b) the v x v slice M[c][d] is combined
+// with its transpose, M[c][d] +- M[d][c]. One block per (al, b, 32 x 32 tile pair (cb <= db)): both tiles
+// are read coalesced into shared memory, and the packed rows (c fastest for fixed d, as tri_le(c, d)
+// runs) are written coalesced.
 template <bool BF16>
-__global__ void k_pack_vvvv(const double* G, int a0, int na, int v, void* Vp, void* Vm, int Kpp, int Kpm,
+__global__ void k_pack_vvvv(const double* __restrict__ G, int a0, int v, void* Vp, void* Vm, int Kpp, int Kpm,
                             long long plane_p, long long plane_m) {
+  __shared__ double T1[32][33], T2[32][33];  // T1[c][d] = M[cb+c][db+d], T2[d][c] = M[db+d][cb+c]
+  const int al = blockIdx.z, b = blockIdx.y, a = a0 + al;
+  if (a > b) return;
+  // tile pair index -> (cb, db) with cb <= db over T = ceil(v / 32) tiles
+  int tp = blockIdx.x, cbt = 0;
+  const int T = (v + 31) / 32;
+  while (tp >= T - cbt) {
+    tp -= T - cbt;
+    ++cbt;
+  }
+  const int cb = 32 * cbt, db = 32 * (cbt + tp);
   const long long vv = static_cast<long long>(v) * v;
-  const long long total = static_cast<long long>(na) * vv * v;  // (a, b, c) then loop d
-  GRID_STRIDE(idx, static_cast<long long>(na) * vv * v) {
-    const int d = idx % v, c = (idx / v) % v, b = (idx / vv) % v, al = idx / (vv * v);
-    const int a = a0 + al;
-    if (a > b || c > d) continue;
-    const double acbd = G[((static_cast<long long>(al) * v + c) * v + b) * v + d];
-    const double adbc = G[((static_cast<long long>(al) * v + d) * v + b) * v + c];
-    const long long pp = static_cast<long long>(tri_le(a, b)) * Kpp + tri_le(c, d);
+  const double* Mb = G + (static_cast<long long>(al) * v * vv + b * static_cast<long long>(v));  // M[c][d] = Mb[c*vv + d]
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int c1 = cb + r, d1 = db + tx;
+    T1[r][tx] = (c1 < v && d1 < v) ? Mb[c1 * vv + d1] : 0.0;
+    const int d2 = db + r, c2 = cb + tx;
+    T2[r][tx] = (d2 < v && c2 < v) ? Mb[d2 * vv + c2] : 0.0;
+  }
+  __syncthreads();
+  const long long rowp = static_cast<long long>(tri_le(a, b)) * Kpp;
+  const long long rowm = a < b ? static_cast<long long>(tri_lt(a, b)) * Kpm : -1;
+  for (int r = ty; r < 32; r += 8) {
+    const int d = db + r, c = cb + tx;
+    if (d >= v || c >= v || c > d) continue;
+    const double acbd = T1[tx][r], adbc = T2[r][tx];
     const double xp = acbd + adbc;
+    const long long pp = rowp + tri_le(c, d);
     if (BF16) {
       __nv_bfloat16 hi, lo;
       split_bf16(xp, hi, lo);
@@ -348,9 +371,9 @@ __global__ void k_pack_vvvv(const double* G, int a0, int na, int v, void* Vp, vo
     } else {
       static_cast<double*>(Vp)[pp] = xp;
     }
-    if (a < b && c < d) {
+    if (rowm >= 0 && c < d) {
       const double xm = acbd - adbc;
-      const long long pm = static_cast<long long>(tri_lt(a, b)) * Kpm + tri_lt(c, d);
+      const long long pm = rowm + tri_lt(c, d);
       if (BF16) {
         __nv_bfloat16 hi, lo;
         split_bf16(xm, hi, lo);
@@ -361,7 +384,6 @@ __global__ void k_pack_vvvv(const double* G, int a0, int na, int v, void* Vp, vo
       }
     }
   }
-  (void)total;
 }
 
 // Dense n x n dressing matrices: X = 1 - T, Y = 1 + T with T[o+a][i] = t_i^a.
@@ -522,12 +544,13 @@ void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s) 
 }
 void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s) {
   const long long pp = 1LL * Vp.rows * Vp.Kp, pm = 1LL * Vm.rows * Vm.Kp;
-  const long long total = 1LL * na * v * v * v;
+  const int T = (v + 31) / 32;
+  dim3 grid(T * (T + 1) / 2, v, na);
   count_launch();
   if (Vp.bf16)
-    k_pack_vvvv<true><<<grid_for(total), kThreads, 0, s>>>(G, a0, na, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+    k_pack_vvvv<true><<<grid, 256, 0, s>>>(G, a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
   else
-    k_pack_vvvv<false><<<grid_for(total), kThreads, 0, s>>>(G, a0, na, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+    k_pack_vvvv<false><<<grid, 256, 0, s>>>(G, a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
 }
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s) {
   count_launch();

@@ -272,6 +272,9 @@ __device__ __forceinline__ void store_out(const OutMap& C, int m, int n, double 
 // ------------------------------------------------------------------------------------------------
 // FP64 SIMT GEMM: 64x64 tile, 16-wide K steps, 256 threads with 4x4 outputs each.
 // ------------------------------------------------------------------------------------------------
+// SYM: C = A A^T (B == A, M == N): only tiles on or above the diagonal run, and off-diagonal tiles
+// also store their mirror image, which halves the work of a symmetric product.
+template <bool SYM>
 __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, const double* __restrict__ B,
                                                   int M, int N, int Kp, OutMap C, int ksplit, double* ws,
                                                   const BatchEntry* __restrict__ batch, int seg) {
@@ -279,6 +282,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, 
   __shared__ double Bs[16][64 + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+  if (SYM && blockIdx.x > blockIdx.y) return;
   long long cbase = 0;
   int kbeg = blockIdx.z * ksplit, kend = min(Kp, kbeg + ksplit);
   if (batch) {  // one problem per blockIdx.z; no split-K
@@ -347,6 +351,15 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, 
         else
           C.dst[off[i][j]] = r;
       }
+  if (SYM && blockIdx.x != blockIdx.y) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) store_out(C, n, m, acc[i][j]);
+      }
+  }
 }
 
 // Fixed-order sum of split-K partials ws[split][M][N], then the OutMap store.
@@ -395,9 +408,20 @@ void gemm_f64(const Packed& A, const Packed& B, int M, int N, int K, const OutMa
   const int nsplit = splits > 1 ? (A.Kp + per - 1) / per : 1;
   dim3 grid((M + 63) / 64, (N + 63) / 64, nsplit);
   count_launch();
-  k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), M, N, A.Kp, C,
+  k_gemm_f64<false><<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(B.p), M, N, A.Kp, C,
                                   per, nsplit > 1 ? split_ws().p : nullptr, nullptr, 0);
   if (nsplit > 1) splitk_reduce(nsplit, M, N, C, s);
+}
+
+void gemm_f64_sym(const Packed& A, int M, const OutMap& C, cudaStream_t s) {
+  if (M <= 0) return;
+  GemmStats& st = gemm_stats();
+  st.launches++;
+  st.flops += 1.0 * M * M * A.Kp;  // half of 2 M^2 K
+  dim3 grid((M + 63) / 64, (M + 63) / 64, 1);
+  count_launch();
+  k_gemm_f64<true><<<grid, 256, 0, s>>>(static_cast<const double*>(A.p), static_cast<const double*>(A.p), M, M, A.Kp,
+                                        C, A.Kp, nullptr, nullptr, 0);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1068,13 +1092,13 @@ void gemm2_batched(const Packed& A0, const Packed& B0, const Packed* A1, const P
   } else {
     dim3 grid((maxM + 63) / 64, (N + 63) / 64, nbatch);
     count_launch();
-    k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A0.p), static_cast<const double*>(B0.p), maxM, N,
+    k_gemm_f64<false><<<grid, 256, 0, s>>>(static_cast<const double*>(A0.p), static_cast<const double*>(B0.p), maxM, N,
                                     A0.Kp, C, A0.Kp, nullptr, dbatch, 0);
     if (A1) {
       OutMap C1 = C;
       C1.beta = 1.0;
       count_launch();
-      k_gemm_f64<<<grid, 256, 0, s>>>(static_cast<const double*>(A1->p), static_cast<const double*>(B1->p), maxM, N,
+      k_gemm_f64<false><<<grid, 256, 0, s>>>(static_cast<const double*>(A1->p), static_cast<const double*>(B1->p), maxM, N,
                                       A1->Kp, C1, A1->Kp, nullptr, dbatch, 1);
     }
   }

@@ -83,6 +83,8 @@ void pack_cols(const View& v, Packed& full, int row0, int col0, int width, cudaS
 // dst[r*K + k] = view(r, k) + beta * dst[r*K + k]   (FP64, no padding)
 void permute(const View& v, double* dst, double beta, cudaStream_t s);
 void gemm_f64(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s);
+// C = A A^T in FP64 with the symmetric half computed once and mirrored (A FP64-packed, M rows)
+void gemm_f64_sym(const Packed& A, int M, const OutMap& C, cudaStream_t s);
 void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,
              cudaStream_t s, int* dstatus);
 // rows [a_row0, a_row0 + M) of A against rows [b_row0, b_row0 + N) of B

@@ -8,9 +8,9 @@
 // once (2 o^3 v^4 + 2 o^4 v^3 flops in the contractions), and the projection over (i, i') stays
 // local to the block.
 //
-// Within a slab of fixed b (virtual c >= b in chunks that fit the L2, a <= b) each of the six
-// permutation terms is one GEMM whose d-part (K = v) and l-part (K = o) accumulate in the same
-// tensor-memory tile (listed per fixed (b, c); rows run over a and one or two occupied indices):
+// Within a slab of fixed b (virtual c >= b in chunks of up to 768 MB of W, a <= b) each of the six
+// permutation terms is one GEMM over K = v + o: the d-part (K = v) and the l-part (K = o) operands are
+// packed side by side along K (listed per fixed (b, c); rows run over a and one or two occupied indices):
 //   G_i  rows (a,i), cols (k,j): (ai|bd) t_kj^cd + (ai|cd) t_jk^bd - t_il^ab (ck|jl) - t_il^ac (bj|kl)
 //   G_j  rows (a,j), cols (k,i): (bj|ad) t_ki^cd - t_jl^ba (ck|il)
 //   G_k  rows (a,k), cols (j,i): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
@@ -183,8 +183,10 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   __syncthreads();
   const TW* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
   // W is stored [i][k][j] (j fastest): read it in that order (coalesced)
-  for (int idx = threadIdx.x; idx < o3; idx += blockDim.x) {
-    const int y1 = idx % o, y2 = (idx / o) % o, y0 = idx / o2;
+  // (y0, y2, y1) of idx advance by the fixed stride blockDim.x with carries: no division in the loop
+  const int st = blockDim.x, d1 = st % o, d2 = (st / o) % o, d0 = st / o2;
+  int y1 = threadIdx.x % o, y2 = (threadIdx.x / o) % o, y0 = threadIdx.x / o2;
+  for (int idx = threadIdx.x; idx < o3; idx += st) {
     const Real Wv = static_cast<Real>(Wb[idx]);
     const Real disc = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
     const Real d = dm[y0] + dm[y1] + dm[y2];
@@ -196,6 +198,13 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
     const int sidx = y0 * S0 + y1 * S1 + y2;
     sw[sidx] = Wv * sc;
     if (!VFLY) sv[sidx] = (Wv + disc) * sc;
+    y1 += d1;
+    int cy = y1 >= o;
+    y1 -= cy ? o : 0;
+    y2 += d2 + cy;
+    cy = y2 >= o;
+    y2 -= cy ? o : 0;
+    y0 += d0 + cy;
   }
   __syncthreads();
   // The six placements of (i, j, k) into the slots of W^{abc}_y: placement q puts i in slot PM[q][0],
