@@ -364,25 +364,30 @@ int Frag::build_consts(bool bf) {
     // ---- packed ladder integrals V+- from G[a][c][b][d] = (ac|bd), chunks of a
     c.Vp = alloc_packed(np_v, np_v, bf);
     c.Vm = alloc_packed(std::max(nm_v, 1), std::max(nm_v, 1), bf);
-    int ac = static_cast<int>(std::max(1LL, std::min<long long>(v, (1LL << 27) / per_k)));
-    double* gtmp = static_cast<double*>(alloc(static_cast<size_t>(ac) * per_k * 8));
+    // G chunks in FP32 on the mixed path (V+- are then split to BF16 hi/lo: FP32 carries more bits
+    // than they keep), FP64 on the FP64 path; chunks of a of about 1 GB
+    const size_t gsz = bf ? 4 : 8;
+    int ac = static_cast<int>(std::max(1LL, std::min<long long>(v, (1LL << 30) / (per_k * static_cast<long long>(gsz)))));
+    void* gtmp = alloc(static_cast<size_t>(ac) * per_k * gsz);
     if (!gtmp || oom) {
       set_error("device allocation failed (vvvv chunk)");
       return LNOCC_ENOMEM;
     }
     for (int a0 = 0; a0 < v; a0 += ac) {
       const int na = std::min(ac, v - a0);
+      OutMap gm = out_rowmajor(bf ? nullptr : static_cast<double*>(gtmp), vv);
+      if (bf) gm.dst32 = static_cast<float*>(gtmp);
       contract_packed_b(view(Bvv + static_cast<long long>(a0) * v, kOne, kOne, A(na * v, 1), kOne, kOne, A(N, vv)),
-                        PBvv, static_cast<int>(vv), out_rowmajor(gtmp, vv));
-      launch_pack_vvvv(gtmp, a0, na, v, c.Vp, c.Vm, s);
+                        PBvv, static_cast<int>(vv), gm);
+      launch_pack_vvvv(gtmp, bf, a0, na, v, c.Vp, c.Vm, s);
     }
     if (!pool) LN_CUDA(cudaStreamSynchronize(s));
     // the chunk temporaries are released right away
-    for (void* p : {static_cast<void*>(tmp), static_cast<void*>(gtmp), PBvv.p}) {
+    for (void* p : {static_cast<void*>(tmp), gtmp, PBvv.p}) {
       dev_free(p);
       allocs.erase(std::find(allocs.begin(), allocs.end(), p));
     }
-    device_bytes -= static_cast<long long>(kc) * per_k * 8 + static_cast<long long>(ac) * per_k * 8 +
+    device_bytes -= static_cast<long long>(kc) * per_k * 8 + static_cast<long long>(ac) * per_k * static_cast<long long>(gsz) +
                     static_cast<long long>(vv) * round_up(N, 64) * (bf ? 4 : 8);
   }
   mixed = keep;

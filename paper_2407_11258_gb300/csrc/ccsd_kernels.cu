@@ -331,8 +331,8 @@ __global__ void k_pair_L(const double* ovov, double* L, int o, int v) {
 // with its transpose, M[c][d] +- M[d][c]. One block per (al, b, 32 x 32 tile pair (cb <= db)): both tiles
 // are read coalesced into shared memory, and the packed rows (c fastest for fixed d, as tri_le(c, d)
 // runs) are written coalesced.
-template <bool BF16>
-__global__ void k_pack_vvvv(const double* __restrict__ G, int a0, int v, void* Vp, void* Vm, int Kpp, int Kpm,
+template <bool BF16, typename TG>
+__global__ void k_pack_vvvv(const TG* __restrict__ G, int a0, int v, void* Vp, void* Vm, int Kpp, int Kpm,
                             long long plane_p, long long plane_m) {
   __shared__ double T1[32][33], T2[32][33];  // T1[c][d] = M[cb+c][db+d], T2[d][c] = M[db+d][cb+c]
   const int al = blockIdx.z, b = blockIdx.y, a = a0 + al;
@@ -346,13 +346,13 @@ __global__ void k_pack_vvvv(const double* __restrict__ G, int a0, int v, void* V
   }
   const int cb = 32 * cbt, db = 32 * (cbt + tp);
   const long long vv = static_cast<long long>(v) * v;
-  const double* Mb = G + (static_cast<long long>(al) * v * vv + b * static_cast<long long>(v));  // M[c][d] = Mb[c*vv + d]
+  const TG* Mb = G + (static_cast<long long>(al) * v * vv + b * static_cast<long long>(v));  // M[c][d] = Mb[c*vv + d]
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   for (int r = ty; r < 32; r += 8) {
     const int c1 = cb + r, d1 = db + tx;
-    T1[r][tx] = (c1 < v && d1 < v) ? Mb[c1 * vv + d1] : 0.0;
+    T1[r][tx] = (c1 < v && d1 < v) ? static_cast<double>(Mb[c1 * vv + d1]) : 0.0;
     const int d2 = db + r, c2 = cb + tx;
-    T2[r][tx] = (d2 < v && c2 < v) ? Mb[d2 * vv + c2] : 0.0;
+    T2[r][tx] = (d2 < v && c2 < v) ? static_cast<double>(Mb[d2 * vv + c2]) : 0.0;
   }
   __syncthreads();
   const long long rowp = static_cast<long long>(tri_le(a, b)) * Kpp;
@@ -542,15 +542,19 @@ void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s) 
   count_launch();
   k_pair_L<<<grid_for(1LL * o * o * v * v), kThreads, 0, s>>>(ovov, L, o, v);
 }
-void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s) {
+void launch_pack_vvvv(const void* G, bool g32, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s) {
   const long long pp = 1LL * Vp.rows * Vp.Kp, pm = 1LL * Vm.rows * Vm.Kp;
   const int T = (v + 31) / 32;
   dim3 grid(T * (T + 1) / 2, v, na);
   count_launch();
-  if (Vp.bf16)
-    k_pack_vvvv<true><<<grid, 256, 0, s>>>(G, a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+  if (Vp.bf16 && g32)
+    k_pack_vvvv<true, float><<<grid, 256, 0, s>>>(static_cast<const float*>(G), a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+  else if (Vp.bf16)
+    k_pack_vvvv<true, double><<<grid, 256, 0, s>>>(static_cast<const double*>(G), a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp,
+                                                   pm);
   else
-    k_pack_vvvv<false><<<grid, 256, 0, s>>>(G, a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp, pm);
+    k_pack_vvvv<false, double><<<grid, 256, 0, s>>>(static_cast<const double*>(G), a0, v, Vp.p, Vm.p, Vp.Kp, Vm.Kp, pp,
+                                                    pm);
 }
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s) {
   count_launch();

@@ -26,7 +26,8 @@ void launch_diis_step(const double* x_new, const double* e_new, double* xs, doub
 void launch_project(const double* E, const double* U, int o, int nlo, double* out, cudaStream_t s);
 void launch_pair_dots(const double* tau, const double* L, int o, long long K, double* E, cudaStream_t s);
 void launch_pair_L(const double* ovov, double* L, int o, int v, cudaStream_t s);
-void launch_pack_vvvv(const double* G, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s);
+// G[al][c][b][d] = (a0+al c|b d), FP32 (g32) or FP64 -> packed V+- rows (a <= b)
+void launch_pack_vvvv(const void* G, bool g32, int a0, int na, int v, Packed& Vp, Packed& Vm, cudaStream_t s);
 void launch_dress_mats(const double* t1, double* X, double* Y, int o, int v, cudaStream_t s);
 void launch_hhat(const double* h, const double* t1, double* g, double* out, int o, int v, cudaStream_t s);
 void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_t s);
