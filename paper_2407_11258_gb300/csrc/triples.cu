@@ -471,7 +471,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     long long tab, part;
   };
   std::vector<Chunk> plan;
-  std::vector<BatchEntry> hbat;
+  std::vector<BatchEntry> hbat, hbat12;  // per-c tables: sigma5 (and rows for sigma2) / merged sigma1 + sigma2
   {
     long long part = 0;
     for (int b = 0; b < v; ++b) {
@@ -485,18 +485,23 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
           const int arow = (c0 + q) * v * o;           // rows (c, a, .) of X1 / T2x / X2 / T2y
           const int brow = b * static_cast<int>(oo);  // rows (b, ., .) of TvT / O1T / Tv / O1
           hbat.push_back(BatchEntry{arow, brow, Ma, arow, brow, 0, q * slab});
+          // sigma1 (rows (b, a, i) of XT1 against rows (c, k, j) of TO) then sigma2 (rows (c, a, i) of XT1
+          // against rows (b, k, j) of TOT): the same (a,i) x (k,j) block of W[c], one accumulator
+          hbat12.push_back(BatchEntry{b * v * o, (c0 + q) * static_cast<int>(oo), Ma, arow, brow, 0, q * slab});
         }
         part += 1LL * (b + 1) * nc;
       }
     }
   }
   BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * std::max<size_t>(hbat.size(), 1)));
-  if (!W || !tpart || !dbat) {
+  BatchEntry* dbat12 = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * std::max<size_t>(hbat12.size(), 1)));
+  if (!W || !tpart || !dbat || !dbat12) {
     cleanup();
     set_error("lnocc_triples: device allocation failed (W chunk)");
     return LNOCC_ENOMEM;
   }
   cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dbat12, hbat12.data(), sizeof(BatchEntry) * hbat12.size(), cudaMemcpyHostToDevice, s);
 
   const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
   const long long small_smem = (3LL * o * (o + 1) + 4LL * o + 8LL * o) * wsz;
@@ -603,12 +608,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     // W layout [c - c0][a][i][k][j]; each term is one contraction over K = v + o (d-part, then l-part).
-    // sigma1: rows (a,i), cols (c,k,j): (ai|bd) t_kj^cd - t_il^ab (ck|jl)   [first writer]
+    // sigma1 + sigma2 (batched over c, two K segments into one accumulator; first writer of W):
+    // rows (a,i), cols (k,j): (ai|bd) t_kj^cd - t_il^ab (ck|jl) + (ai|cd) t_jk^bd - t_il^ac (bj|kl)
     {
       OutMap m = omap(0.0);
       m.sm1 = ooo; m.sm0 = oo; m.mdiv = o;
-      m.sn2 = Sc; m.sn1 = o; m.sn0 = 1; m.ndiv = o; m.ndiv1 = o;
-      gemm_off(XT1, xb, TO, c0 * o2, Ma, nc * o2, Kt, m, s, dstatus);
+      m.sn1 = o; m.sn0 = 1; m.ndiv = o;
+      gemm2_batched(XT1, TO, &XT1, &TOT, dbat12 + ch.tab, nc, Ma, o2, Kt, Kt, m, s, dstatus);
     }
     // sigma3: rows (a,j), cols (c,k,i): (bj|ad) t_ki^cd - t_jl^ba (ck|il)
     {
@@ -630,13 +636,6 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       m.sm2 = ooo; m.sm1 = oo; m.sm0 = 1; m.mdiv = o; m.mdiv1 = o;
       m.sn1 = Sc; m.sn0 = o; m.ndiv = o;
       gemm_off(TO, 0, XT1, xb + c0 * o, Ma2, nc * o, Kt, m, s, dstatus);
-    }
-    // sigma2 (batched over c): rows (a,i), cols (k,j): (ai|cd) t_jk^bd - t_il^ac (bj|kl)
-    {
-      OutMap m = omap(1.0);
-      m.sm1 = ooo; m.sm0 = oo; m.mdiv = o;
-      m.sn1 = o; m.sn0 = 1; m.ndiv = o;
-      gemm_batched(XT1, TOT, dbat + ch.tab, nc, Ma, o2, Kt, m, s, dstatus);
     }
     // sigma5 (batched over c): rows (a,k), cols (i,j): (ck|ad) t_ji^bd - t_kl^ca (bj|il)
     // (TOT[b][i][j] = [t_ji^bd | (bj|il)]: j runs fastest in the columns)
