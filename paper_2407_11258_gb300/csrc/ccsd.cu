@@ -532,8 +532,11 @@ void Frag::iterate(bool fp64_residual) {
   permute(view(Fh, kOne, kOne, A(o, n), kOne, kOne, A(o, 1)), Foo2, 0.0, s);
   // Mtmp[Q][d][i] = sum_kc B_Qkc u_ki^cd (shared with the singles term A1);
   // sum_lcd u_lj^cd (kd|lc) = sum_{Q,d} B_Qkd Mtmp[Q][d][j]
+  // (u rows taken as (i, d) with d contiguous so that the operand pack reads coalesced; the output
+  // columns (i, d) land at Mtmp[Q][d][i])
   contract(view(Bov, kOne, kOne, A(N, ov), kOne, kOne, A(static_cast<int>(ov), 1)),
-           view(u, kOne, A(v, 1), A(o, vv), kOne, A(o, o * vv), A(v, v)), out_rowmajor(Mtmp, ov));
+           view(u, kOne, A(o, vv), A(v, 1), kOne, A(o, o * vv), A(v, v)),
+           OutMap{Mtmp, 0, ov, 1, o, 1 << 30, v, 1.0, 0.0});
   contract(view(Bov, kOne, kOne, A(o, v), kOne, A(N, ov), A(v, 1)),
            view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)), out_rowmajor(Foo2, o, 1.0, 1.0));
   mark("Foo");

@@ -83,33 +83,58 @@ __global__ void k_pack(View v, void* out, int Kw, int ld, long long plane) {
     const double* src = v.src + view_roff(v, r);
     const long long base = static_cast<long long>(r) * ld;
     const int kend = min(Kw, (ch + 1) * 256);
-    for (int k = ch * 256 + lane; k < kend; k += 32) {
-      double x = 0.0;
-      if (k < K) x = v.scale * src[kflat ? static_cast<long long>(k) * v.sk0 : view_koff(v, k)];
-      put<BF16>(out, base + k, plane, x);
+    // all eight loads of the lane first (independent, in flight together), then the stores
+    double x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = ch * 256 + lane + 32 * t;
+      x[t] = (k < K && k < kend) ? v.scale * src[kflat ? static_cast<long long>(k) * v.sk0 : view_koff(v, k)] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = ch * 256 + lane + 32 * t;
+      if (k < kend) put<BF16>(out, base + k, plane, x[t]);
     }
   }
 }
 
 // Transposing pack for sources whose rows are contiguous (sr0 == 1) and K is strided:
 // 32 x 32 tiles through shared memory so that both the reads and the writes are coalesced.
+// Blocks walk the 32 x 32 tiles grid-stride (few, long-lived blocks); a tile wholly beyond K is
+// written as zeros without reading.
 template <bool BF16>
 __global__ void k_pack_t(View v, void* out, int Kw, int ld, long long plane) {
   __shared__ double tile[32][33];
   const int K = v.K2 * v.K1 * v.K0;
   const int rows = v.R2 * v.R1 * v.R0;
-  const int rb = blockIdx.x * 32, kb = blockIdx.y * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
-  for (int ky = ty; ky < 32; ky += 8) {
-    const int r = rb + tx, k = kb + ky;
-    double x = 0.0;
-    if (r < rows && k < K) x = v.scale * v.src[view_off(v, r, k)];
-    tile[ky][tx] = x;
-  }
-  __syncthreads();
-  for (int ry = ty; ry < 32; ry += 8) {
-    const int r = rb + ry, k = kb + tx;
-    if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ry]);
+  const int nrt = (rows + 31) / 32, nkt = (Kw + 31) / 32;
+  const long long ntiles = static_cast<long long>(nrt) * nkt;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int rb = static_cast<int>(t / nkt) * 32, kb = static_cast<int>(t % nkt) * 32;
+    if (kb < K) {
+      double x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = rb + tx, k = kb + ty + 8 * q;
+        x[q] = (r < rows && k < K) ? v.scale * v.src[view_off(v, r, k)] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tile[ty + 8 * q][tx] = x[q];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = rb + ty + 8 * q, k = kb + tx;
+        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ty + 8 * q]);
+      }
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = rb + ty + 8 * q, k = kb + tx;
+        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, 0.0);
+      }
+    }
   }
 }
 
@@ -118,7 +143,8 @@ static void launch_pack(const View& v, void* out, int Kw, int ld, long long plan
   const bool transpose = v.sr0 == 1 && v.R0 >= 32 && (v.sk0 != 1);
   count_launch();
   if (transpose) {
-    dim3 grid((rows + 31) / 32, (Kw + 31) / 32);
+    const long long tiles = static_cast<long long>((rows + 31) / 32) * ((Kw + 31) / 32);
+    const int grid = static_cast<int>(std::min<long long>(tiles, 152LL * 8));
     if (bf16)
       k_pack_t<true><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
     else
