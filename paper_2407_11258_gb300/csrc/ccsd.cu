@@ -438,15 +438,23 @@ void Frag::iterate(bool fp64_residual) {
            view(t1, kOne, kOne, A(o, v), kOne, kOne, A(v, 1)), out_rowmajor(Boo_h, o, 1.0, 1.0));
   // B^_vo[Q][a][i] = B_ov[Q][i][a] + sum_c B_vv[Q][a][c] t_i^c - sum_k t_k^a B^_oo[Q][k][i]
   permute(view(Bov, kOne, A(N, ov), A(v, 1), kOne, kOne, A(o, v)), Bvo_h, 0.0, s);
-  contract(view(Bvv, kOne, kOne, A(static_cast<int>(N * v), v), kOne, kOne, A(v, 1)),
-           view(t1, kOne, kOne, A(o, v), kOne, kOne, A(v, 1)), out_rowmajor(Bvo_h, o, 1.0, 1.0));
+  // mixed path: B^_vv and the B_vv t1 part of B^_vo in one streaming pass over B_vv
+  const bool fused_vv = mixed && o <= 32 && v <= 850;
+  if (fused_vv) {
+    launch_dress_vv(Bvv, Bov, t1, Bvv_h, Bvo_h, N, o, v, s);
+  } else {
+    contract(view(Bvv, kOne, kOne, A(static_cast<int>(N * v), v), kOne, kOne, A(v, 1)),
+             view(t1, kOne, kOne, A(o, v), kOne, kOne, A(v, 1)), out_rowmajor(Bvo_h, o, 1.0, 1.0));
+  }
   contract(view(t1, kOne, kOne, A(v, 1), kOne, kOne, A(o, v)),
            view(Boo_h, kOne, A(N, oo), A(o, 1), kOne, kOne, A(o, o)),
            OutMap{Bvo_h, 0, o, ov, 1, 1 << 30, o, -1.0, 1.0});
   // B^_vv[Q][a][c] = B_vv - sum_k t_k^a B_ov[Q][k][c]
-  cudaMemcpyAsync(Bvv_h, Bvv, N * vv * 8, cudaMemcpyDeviceToDevice, s);
-  contract(view(t1, kOne, kOne, A(v, 1), kOne, kOne, A(o, v)), view(Bov, kOne, A(N, ov), A(v, 1), kOne, kOne, A(o, v)),
-           OutMap{Bvv_h, 0, v, vv, 1, 1 << 30, v, -1.0, 1.0});
+  if (!fused_vv) {
+    cudaMemcpyAsync(Bvv_h, Bvv, N * vv * 8, cudaMemcpyDeviceToDevice, s);
+    contract(view(t1, kOne, kOne, A(v, 1), kOne, kOne, A(o, v)),
+             view(Bov, kOne, A(N, ov), A(v, 1), kOne, kOne, A(o, v)), OutMap{Bvv_h, 0, v, vv, 1, 1 << 30, v, -1.0, 1.0});
+  }
 
   pack_df();
   const Consts& K = C();
@@ -540,9 +548,12 @@ void Frag::iterate(bool fp64_residual) {
   contract(view(Bov, kOne, kOne, A(o, v), kOne, A(N, ov), A(v, 1)),
            view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)), out_rowmajor(Foo2, o, 1.0, 1.0));
   mark("Foo");
-  contract(view(t2, kOne, A(o, o * vv), A(static_cast<int>(vv), 1), kOne, kOne, A(o, vv)),
-           view(Foo2, kOne, kOne, A(o, 1), kOne, kOne, A(o, o)), OutMap{S, o * vv, 1, 0, vv, static_cast<int>(vv),
-                                                                       1 << 30, -1.0, 1.0});
+  if (mixed && o <= 32)
+    launch_e2_occ(t2, Foo2, S, o, v, s);  // length-o contraction: one streaming pass
+  else
+    contract(view(t2, kOne, A(o, o * vv), A(static_cast<int>(vv), 1), kOne, kOne, A(o, vv)),
+             view(Foo2, kOne, kOne, A(o, 1), kOne, kOne, A(o, o)),
+             OutMap{S, o * vv, 1, 0, vv, static_cast<int>(vv), 1 << 30, -1.0, 1.0});
   mark("E2b");
   // C2 intermediate X_kiac = g^_kiac - 1/2 sum_dl t_li^ad (kd|lc), stored [k][i][a][c]
   gemm(K.PBoo, K.PBvv, static_cast<int>(oo), static_cast<int>(vv), N, out_rowmajor(Xk, vv), s, dstatus);

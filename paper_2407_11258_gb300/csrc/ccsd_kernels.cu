@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ccsd_kernels.h"
 #include "ptx.cuh"
 
@@ -467,6 +469,88 @@ __global__ void k_finite(const double* x, long long n, int* flag) {
   }
 }
 
+// E2 occupied part, S[i][j][ab] -= sum_k t2[i][k][ab] F[k][j] (nocc <= 32): a contraction of length
+// nocc is bound by the traffic of t2 and S, so it runs as one streaming pass with FP32 products and
+// sums (relative error ~1e-7, below the BF16x3 contractions of the mixed path) instead of a padded GEMM.
+template <int MAXO>
+__global__ void k_e2_occ(const double* __restrict__ t2, const double* __restrict__ F, double* __restrict__ S, int o,
+                         long long vv) {
+  __shared__ float Fs[32][33];
+  for (int x = threadIdx.x; x < 32 * 32; x += blockDim.x) {
+    const int k = x / 32, j = x % 32;
+    Fs[k][j] = (k < o && j < o) ? static_cast<float>(F[k * o + j]) : 0.f;
+  }
+  __syncthreads();
+  const long long total = static_cast<long long>(o) * vv;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long i = e / vv, ab = e % vv;
+    float t[MAXO];
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) t[k] = k < o ? static_cast<float>(t2[(i * o + k) * vv + ab]) : 0.f;
+    for (int j = 0; j < o; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < MAXO; ++k) acc = fmaf(t[k], Fs[k][j], acc);
+      S[(i * o + j) * vv + ab] -= static_cast<double>(acc);
+    }
+  }
+}
+
+// T1 dressing of the virtual-virtual DF block in one pass over B_vv (mixed path, nocc <= 32): per row
+// (Q, a), with t1 and B_ov[Q] staged in shared memory,
+//   B^_vv[Q][a][c] = B_vv[Q][a][c] - sum_k t_k^a B_ov[Q][k][c]
+//   B^_vo[Q][a][i] += sum_c B_vv[Q][a][c] t_i^c
+// Both corrections are length-o / length-v dot products on data read once, so the pass is bound by the
+// traffic of B_vv (read) and B^_vv (written); products and sums in FP32 (relative error ~1e-7),
+// the dressed factors stay FP64. One warp per row; the v-sums end in a fixed-order warp butterfly.
+template <int MAXO>
+__global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restrict__ Bov,
+                           const double* __restrict__ t1, double* __restrict__ Bvv_h, double* __restrict__ Bvo_h,
+                           int o, int v) {
+  extern __shared__ float dsm[];
+  float* ts = dsm;                    // t1[k][c], o x v
+  float* bs = dsm + MAXO * v;         // B_ov[Q][k][c], o x v
+  const int Q = blockIdx.x;
+  const long long ov = static_cast<long long>(o) * v, vv = static_cast<long long>(v) * v;
+  for (int x = threadIdx.x; x < o * v; x += blockDim.x) {
+    ts[x] = static_cast<float>(t1[x]);
+    bs[x] = static_cast<float>(Bov[Q * ov + x]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int a = warp; a < v; a += nw) {
+    float ta[MAXO], acc[MAXO];
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+      ta[k] = k < o ? ts[k * v + a] : 0.f;
+      acc[k] = 0.f;
+    }
+    const double* row = Bvv + Q * vv + static_cast<long long>(a) * v;
+    double* orow = Bvv_h + Q * vv + static_cast<long long>(a) * v;
+    for (int c = lane; c < v; c += 32) {
+      const double x = row[c];
+      const float xf = static_cast<float>(x);
+      float corr = 0.f;
+#pragma unroll
+      for (int k = 0; k < MAXO; ++k)
+        if (k < o) {
+          corr = fmaf(ta[k], bs[k * v + c], corr);
+          acc[k] = fmaf(xf, ts[k * v + c], acc[k]);
+        }
+      orow[c] = x - static_cast<double>(corr);
+    }
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    double* vo = Bvo_h + Q * ov + static_cast<long long>(a) * o;
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k)
+      if (k < o && lane == k) vo[k] += static_cast<double>(acc[k]);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // launch wrappers
 void launch_tau(const double* t1, const double* t2, double* tau, int o, int v, cudaStream_t s) {
@@ -574,6 +658,29 @@ void launch_coulomb(const double* B, long long qstride, int rows, int cols, long
   count_launch();
   k_coulomb<<<static_cast<int>((1LL * rows * cols + 31) / 32), 256, 0, s>>>(B, qstride, rows, cols, rstride, x, naux,
                                                                           alpha, dst, ld);
+}
+void launch_dress_vv(const double* Bvv, const double* Bov, const double* t1, double* Bvv_h, double* Bvo_h, int naux,
+                     int o, int v, cudaStream_t s) {
+  static std::once_flag once;  // the attribute is process-wide: set it once, to the largest size used
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_dress_vv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 32 * 850 * 4);
+    cudaFuncSetAttribute(k_dress_vv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 32 * 850 * 4);
+  });
+  count_launch();
+  if (o <= 16) {
+    const size_t sm = 2 * 16 * static_cast<size_t>(v) * 4;
+    k_dress_vv<16><<<naux, 256, sm, s>>>(Bvv, Bov, t1, Bvv_h, Bvo_h, o, v);
+  } else {
+    const size_t sm = 2 * 32 * static_cast<size_t>(v) * 4;
+    k_dress_vv<32><<<naux, 256, sm, s>>>(Bvv, Bov, t1, Bvv_h, Bvo_h, o, v);
+  }
+}
+void launch_e2_occ(const double* t2, const double* F, double* S, int o, int v, cudaStream_t s) {
+  count_launch();
+  if (o <= 16)
+    k_e2_occ<16><<<grid_for(1LL * o * v * v), kThreads, 0, s>>>(t2, F, S, o, 1LL * v * v);
+  else
+    k_e2_occ<32><<<grid_for(1LL * o * v * v), kThreads, 0, s>>>(t2, F, S, o, 1LL * v * v);
 }
 void launch_finite(const double* x, long long n, int* flag, cudaStream_t s) {
   count_launch();

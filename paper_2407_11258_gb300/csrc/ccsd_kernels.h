@@ -34,4 +34,10 @@ void launch_trace_oo(const double* Boo, int naux, int o, double* xq, cudaStream_
 void launch_coulomb(const double* B, long long qstride, int rows, int cols, long long rstride, const double* x,
                     int naux, double alpha, double* dst, long long ld, cudaStream_t s);
 void launch_finite(const double* x, long long n, int* flag, cudaStream_t s);
+// B^_vv = B_vv - t1^T B_ov and B^_vo += B_vv t1^T in one pass over B_vv (nocc <= 32, 2*MAXO*v*4 bytes of
+// shared memory, v <= 1700 for MAXO = 16 / 850 for 32); FP32 products and sums, FP64 results
+void launch_dress_vv(const double* Bvv, const double* Bov, const double* t1, double* Bvv_h, double* Bvo_h, int naux,
+                     int o, int v, cudaStream_t s);
+// S[i][j][a][b] -= sum_k t2[i][k][a][b] F[k][j], nocc <= 32, FP32 products and sums
+void launch_e2_occ(const double* t2, const double* F, double* S, int o, int v, cudaStream_t s);
 }  // namespace lnocc
