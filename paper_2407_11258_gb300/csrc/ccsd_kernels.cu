@@ -529,17 +529,24 @@ __global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restr
     }
     const double* row = Bvv + Q * vv + static_cast<long long>(a) * v;
     double* orow = Bvv_h + Q * vv + static_cast<long long>(a) * v;
-    for (int c = lane; c < v; c += 32) {
-      const double x = row[c];
-      const float xf = static_cast<float>(x);
-      float corr = 0.f;
+    for (int c0 = lane; c0 < v; c0 += 32 * 8) {
+      double xs[8];  // eight independent loads in flight per lane
 #pragma unroll
-      for (int k = 0; k < MAXO; ++k)
-        if (k < o) {
-          corr = fmaf(ta[k], bs[k * v + c], corr);
-          acc[k] = fmaf(xf, ts[k * v + c], acc[k]);
-        }
-      orow[c] = x - static_cast<double>(corr);
+      for (int t = 0; t < 8; ++t) xs[t] = c0 + 32 * t < v ? row[c0 + 32 * t] : 0.0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int c = c0 + 32 * t;
+        if (c >= v) break;
+        const float xf = static_cast<float>(xs[t]);
+        float corr = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAXO; ++k)
+          if (k < o) {
+            corr = fmaf(ta[k], bs[k * v + c], corr);
+            acc[k] = fmaf(xf, ts[k * v + c], acc[k]);
+          }
+        orow[c] = xs[t] - static_cast<double>(corr);
+      }
     }
 #pragma unroll
     for (int k = 0; k < MAXO; ++k)
@@ -575,11 +582,19 @@ __global__ void k_a1(const double* __restrict__ Bvv_h, const double* __restrict_
 #pragma unroll
       for (int k = 0; k < MAXO; ++k) acc[k] = 0.f;
       const double* row = Bvv_h + Q * vv + static_cast<long long>(a) * v;
-      for (int d = lane; d < v; d += 32) {
-        const float x = static_cast<float>(row[d]);
+      for (int d0 = lane; d0 < v; d0 += 32 * 8) {
+        double xs[8];  // eight independent loads in flight per lane
 #pragma unroll
-        for (int k = 0; k < MAXO; ++k)
-          if (k < o) acc[k] = fmaf(x, Ms[d * o + k], acc[k]);
+        for (int t = 0; t < 8; ++t) xs[t] = d0 + 32 * t < v ? row[d0 + 32 * t] : 0.0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int d = d0 + 32 * t;
+          if (d >= v) break;
+          const float x = static_cast<float>(xs[t]);
+#pragma unroll
+          for (int k = 0; k < MAXO; ++k)
+            if (k < o) acc[k] = fmaf(x, Ms[d * o + k], acc[k]);
+        }
       }
 #pragma unroll
       for (int k = 0; k < MAXO; ++k)
