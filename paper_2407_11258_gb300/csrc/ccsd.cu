@@ -580,10 +580,8 @@ void Frag::iterate(bool fp64_residual) {
   mark("D2");
   // ---- singles residual R1[i][a]
   // A1 via DF: R1 += sum_{Q,d} B^_Qad Mtmp[Q][d][i]
-  if (!(mixed && launch_a1(Bvv_h, Mtmp, N, o, v, splitk, splitk_cap, R1, s)))
-    contract(view(Bvv_h, kOne, kOne, A(v, v), kOne, A(N, vv), A(v, 1)),
-             view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)),
-             OutMap{R1, 0, 1, 0, v, 1 << 30, 1 << 30, 1.0, 0.0});
+  contract(view(Bvv_h, kOne, kOne, A(v, v), kOne, A(N, vv), A(v, 1)),
+           view(Mtmp, kOne, kOne, A(o, 1), kOne, A(N, ov), A(v, o)), OutMap{R1, 0, 1, 0, v, 1 << 30, 1 << 30, 1.0, 0.0});
   mark("A1");
   // B1: R1 -= sum_klc u_kl^ac g^_kilc ; g^_kilc stored [i][k][l][c]
   gemm(K.PBoo, K.PBov, static_cast<int>(oo), static_cast<int>(ov), N, OutMap{Gooov, ov, o * ov, 0, 1, o, 1 << 30, 1.0, 0.0},

@@ -559,66 +559,6 @@ __global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restr
   }
 }
 
-// Singles term A1, R1[i][a] = sum_{Q,d} B^_vv[Q][a][d] M[Q][d][i] (nocc <= 32), as one streaming pass
-// over B^_vv: block g takes Q = g, g + G, ...; per Q, M[Q] is staged in shared memory and warp w forms
-// the v-sums of rows a = w, w + 8, ... (FP32 products, fixed-order butterfly), adding them into the
-// block's FP64 partial P[a][i], which that warp alone owns. part[g][a][i] is then summed over g in a
-// fixed order by k_a1_finish.
-template <int MAXO>
-__global__ void k_a1(const double* __restrict__ Bvv_h, const double* __restrict__ M, int naux, int o, int v,
-                     double* __restrict__ part) {
-  extern __shared__ unsigned char a1sm[];
-  double* P = reinterpret_cast<double*>(a1sm);                // [v][o]
-  float* Ms = reinterpret_cast<float*>(P + static_cast<size_t>(v) * o);  // [v][o] (d, i)
-  const long long vv = static_cast<long long>(v) * v, vo = static_cast<long long>(v) * o;
-  for (int x = threadIdx.x; x < v * o; x += blockDim.x) P[x] = 0.0;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int Q = blockIdx.x; Q < naux; Q += gridDim.x) {
-    __syncthreads();
-    for (int x = threadIdx.x; x < v * o; x += blockDim.x) Ms[x] = static_cast<float>(M[Q * vo + x]);
-    __syncthreads();
-    for (int a = warp; a < v; a += nw) {
-      float acc[MAXO];
-#pragma unroll
-      for (int k = 0; k < MAXO; ++k) acc[k] = 0.f;
-      const double* row = Bvv_h + Q * vv + static_cast<long long>(a) * v;
-      for (int d0 = lane; d0 < v; d0 += 32 * 8) {
-        double xs[8];  // eight independent loads in flight per lane
-#pragma unroll
-        for (int t = 0; t < 8; ++t) xs[t] = d0 + 32 * t < v ? row[d0 + 32 * t] : 0.0;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int d = d0 + 32 * t;
-          if (d >= v) break;
-          const float x = static_cast<float>(xs[t]);
-#pragma unroll
-          for (int k = 0; k < MAXO; ++k)
-            if (k < o) acc[k] = fmaf(x, Ms[d * o + k], acc[k]);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < MAXO; ++k)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-#pragma unroll
-      for (int k = 0; k < MAXO; ++k)
-        if (k < o && lane == k) P[a * o + k] += static_cast<double>(acc[k]);
-    }
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < v * o; x += blockDim.x) part[blockIdx.x * vo + x] = P[x];
-}
-__global__ void k_a1_finish(const double* __restrict__ part, int nblk, int o, int v, double* __restrict__ R1) {
-  const long long vo = static_cast<long long>(v) * o;
-  for (long long x = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; x < vo;
-       x += static_cast<long long>(gridDim.x) * blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < nblk; ++g) s += part[g * vo + x];
-    const int a = static_cast<int>(x / o), i = static_cast<int>(x % o);
-    R1[static_cast<long long>(i) * v + a] = s;
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
 // launch wrappers
 void launch_tau(const double* t1, const double* t2, double* tau, int o, int v, cudaStream_t s) {
@@ -742,25 +682,6 @@ void launch_dress_vv(const double* Bvv, const double* Bov, const double* t1, dou
     const size_t sm = 2 * 32 * static_cast<size_t>(v) * 4;
     k_dress_vv<32><<<naux, 256, sm, s>>>(Bvv, Bov, t1, Bvv_h, Bvo_h, o, v);
   }
-}
-bool launch_a1(const double* Bvv_h, const double* M, int naux, int o, int v, double* ws, size_t ws_cap, double* R1,
-               cudaStream_t s) {
-  const size_t sm = static_cast<size_t>(v) * o * 12;
-  int nblk = std::min(naux, 2 * 152);
-  while (nblk > 1 && static_cast<size_t>(nblk) * v * o > ws_cap) nblk /= 2;
-  if (o > 32 || sm > 200 * 1024 || static_cast<size_t>(nblk) * v * o > ws_cap) return false;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(k_a1<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_a1<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  });
-  count_launch(2);
-  if (o <= 16)
-    k_a1<16><<<nblk, 256, sm, s>>>(Bvv_h, M, naux, o, v, ws);
-  else
-    k_a1<32><<<nblk, 256, sm, s>>>(Bvv_h, M, naux, o, v, ws);
-  k_a1_finish<<<grid_for(1LL * v * o), kThreads, 0, s>>>(ws, nblk, o, v, R1);
-  return true;
 }
 void launch_e2_occ(const double* t2, const double* F, double* S, int o, int v, cudaStream_t s) {
   count_launch();

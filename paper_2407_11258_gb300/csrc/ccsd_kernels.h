@@ -38,10 +38,6 @@ void launch_finite(const double* x, long long n, int* flag, cudaStream_t s);
 // shared memory, v <= 1700 for MAXO = 16 / 850 for 32); FP32 products and sums, FP64 results
 void launch_dress_vv(const double* Bvv, const double* Bov, const double* t1, double* Bvv_h, double* Bvo_h, int naux,
                      int o, int v, cudaStream_t s);
-// R1[i][a] = sum_{Q,d} B^_vv[Q][a][d] M[Q][d][i] in one pass over B^_vv (FP32 products, FP64 partials
-// in ws, fixed-order sums); false (nothing launched) when nocc > 32 or ws / shared memory is too small
-bool launch_a1(const double* Bvv_h, const double* M, int naux, int o, int v, double* ws, size_t ws_cap, double* R1,
-               cudaStream_t s);
 // S[i][j][a][b] -= sum_k t2[i][k][a][b] F[k][j], nocc <= 32, FP32 products and sums
 void launch_e2_occ(const double* t2, const double* F, double* S, int o, int v, cudaStream_t s);
 }  // namespace lnocc
