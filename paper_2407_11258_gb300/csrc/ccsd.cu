@@ -300,7 +300,7 @@ int Frag::build(const double* eps_in, const double* B_in) {
   }
   // MP2 energy (iteration 0)
   {
-    const int g = launch_energy(nullptr, t2mp2, ovov, part, o, v, s);
+    const int g = launch_energy(nullptr, t2mp2, Lpair, part, o, v, s);
     launch_finish_sum(part, g, scal, s);
     LN_CUDA(cudaMemcpyAsync(h_scal, scal, 8, cudaMemcpyDeviceToHost, s));
     LN_CUDA(cudaStreamSynchronize(s));
@@ -607,7 +607,7 @@ void Frag::iterate(bool fp64_residual) {
 }
 
 double Frag::energy_of(const double* x) {
-  const int g = launch_energy(x, x + 1LL * o * v, ovov, part, o, v, s);
+  const int g = launch_energy(x, x + 1LL * o * v, Lpair, part, o, v, s);
   launch_finish_sum(part, g, scal, s);
   return 0.0;
 }

@@ -128,23 +128,46 @@ __global__ void k_ladder_unpack(const double* Lp, const double* Lm, double* R, i
 
 // Doubles residual R = Rsym + S + S^(ij)(ab) + P[C2] and update t2n = t2 + R / D.
 // C2_aibj = -1/2 Cp[j,b,i,a] - Cp[i,b,j,a] (Cp[(j,b),(i,a)] = sum_kc t_kj^bc X_kiac).
-__global__ void k_assemble(const double* Rsym, const double* S, const double* Cp, const double* t2, const double* eps,
-                           double* t2n, double* err, double* part, int o, int v) {
-  const long long vv = static_cast<long long>(v) * v;
-  const long long total = static_cast<long long>(o) * o * vv;
-  const long long ov = static_cast<long long>(o) * v;
+// The three operands read with (a, b) exchanged -- S[j][i][b][a], Cp[(j,b)(i,a)], Cp[(i,b)(j,a)] -- go
+// through 32 x 32 shared-memory tiles so that every global access is coalesced. Blocks walk the
+// (i, j, a-tile, b-tile) tiles grid-stride; the per-block partial of sum d^2 is in a fixed order.
+__global__ void k_assemble(const double* __restrict__ Rsym, const double* __restrict__ S, const double* __restrict__ Cp,
+                           const double* __restrict__ t2, const double* __restrict__ eps, double* __restrict__ t2n,
+                           double* __restrict__ err, double* __restrict__ part, int o, int v) {
+  __shared__ double TS[32][33], T1[32][33], T2[32][33];  // [b_local][a_local]
+  const long long vv = static_cast<long long>(v) * v, ov = static_cast<long long>(o) * v;
+  const int nt = (v + 31) / 32;
+  const long long ntiles = static_cast<long long>(o) * o * nt * nt;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   double acc = 0.0;
-  GRID_STRIDE(idx, total) {
-    const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
-    const long long ji_ba = (static_cast<long long>(j) * o + i) * vv + static_cast<long long>(b) * v + a;
-    const double c2 = -0.5 * Cp[(j * v + b) * ov + i * v + a] - Cp[(i * v + b) * ov + j * v + a] -
-                      0.5 * Cp[(i * v + a) * ov + j * v + b] - Cp[(j * v + a) * ov + i * v + b];
-    const double R = Rsym[idx] + S[idx] + S[ji_ba] + c2;
-    const double D = eps[i] + eps[j] - eps[o + a] - eps[o + b];
-    const double d = R / D;
-    t2n[idx] = t2[idx] + d;
-    err[idx] = d;
-    acc += d * d;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int bt = static_cast<int>(t % nt), at = static_cast<int>((t / nt) % nt);
+    const int ij = static_cast<int>(t / (static_cast<long long>(nt) * nt)), j = ij % o, i = ij / o;
+    const int a0 = 32 * at, b0 = 32 * bt;
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int b = b0 + r, a = a0 + tx;
+      const bool ok = a < v && b < v;
+      TS[r][tx] = ok ? S[(static_cast<long long>(j) * o + i) * vv + static_cast<long long>(b) * v + a] : 0.0;
+      T1[r][tx] = ok ? Cp[(static_cast<long long>(j) * v + b) * ov + static_cast<long long>(i) * v + a] : 0.0;
+      T2[r][tx] = ok ? Cp[(static_cast<long long>(i) * v + b) * ov + static_cast<long long>(j) * v + a] : 0.0;
+    }
+    __syncthreads();
+    const double ei_j = eps[i] + eps[j];
+    for (int r = ty; r < 32; r += 8) {
+      const int a = a0 + r, b = b0 + tx;
+      if (a >= v || b >= v) continue;
+      const long long idx = (static_cast<long long>(i) * o + j) * vv + static_cast<long long>(a) * v + b;
+      const double c2 = -0.5 * T1[tx][r] - T2[tx][r] -
+                        0.5 * Cp[(static_cast<long long>(i) * v + a) * ov + static_cast<long long>(j) * v + b] -
+                        Cp[(static_cast<long long>(j) * v + a) * ov + static_cast<long long>(i) * v + b];
+      const double R = Rsym[idx] + S[idx] + TS[tx][r] + c2;
+      const double D = ei_j - eps[o + a] - eps[o + b];
+      const double d = R / D;
+      t2n[idx] = t2[idx] + d;
+      err[idx] = d;
+      acc += d * d;
+    }
   }
   block_sum_store(acc, part);
 }
@@ -165,16 +188,15 @@ __global__ void k_update_t1(const double* R1, const double* Fvo, const double* t
 }
 
 // E = sum_ijab (t_ij^ab + t_i^a t_j^b)(2(ia|jb) - (ib|ja)); OVOV[i][a][j][b] = (ia|jb)
-__global__ void k_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v) {
+// Lpair[i][j][a][b] = 2(ia|jb) - (ib|ja) (k_pair_L): both streams read in the same order (coalesced)
+__global__ void k_energy(const double* t1, const double* t2, const double* Lpair, double* part, int o, int v) {
   const long long vv = static_cast<long long>(v) * v;
   const long long total = static_cast<long long>(o) * o * vv;
   double acc = 0.0;
   GRID_STRIDE(idx, total) {
     const int b = idx % v, a = (idx / v) % v, j = (idx / vv) % o, i = idx / (vv * o);
     const double tau = t2[idx] + (t1 ? t1[i * v + a] * t1[j * v + b] : 0.0);
-    const double iajb = ovov[((static_cast<long long>(i) * v + a) * o + j) * v + b];
-    const double ibja = ovov[((static_cast<long long>(i) * v + b) * o + j) * v + a];
-    acc += tau * (2.0 * iajb - ibja);
+    acc += tau * Lpair[idx];
   }
   block_sum_store(acc, part);
 }
@@ -585,7 +607,8 @@ void launch_ladder_unpack(const double* Lp, const double* Lm, double* R, int o, 
 }
 int launch_assemble(const double* Rsym, const double* S, const double* Cp, const double* t2, const double* eps,
                     double* t2n, double* err, double* part, int o, int v, cudaStream_t s) {
-  const int g = grid_for(1LL * o * o * v * v);
+  const int nt = (v + 31) / 32;
+  const int g = static_cast<int>(std::min<long long>(1LL * o * o * nt * nt, 152LL * 8));
   count_launch();
   k_assemble<<<g, kThreads, 0, s>>>(Rsym, S, Cp, t2, eps, t2n, err, part, o, v);
   return g;
@@ -597,11 +620,11 @@ int launch_update_t1(const double* R1, const double* Fvo, const double* t1, cons
   k_update_t1<<<g, kThreads, 0, s>>>(R1, Fvo, t1, eps, t1n, err, part, o, v);
   return g;
 }
-int launch_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v,
+int launch_energy(const double* t1, const double* t2, const double* Lpair, double* part, int o, int v,
                   cudaStream_t s) {
   const int g = grid_for(1LL * o * o * v * v);
   count_launch();
-  k_energy<<<g, kThreads, 0, s>>>(t1, t2, ovov, part, o, v);
+  k_energy<<<g, kThreads, 0, s>>>(t1, t2, Lpair, part, o, v);
   return g;
 }
 void launch_finish_sum(const double* part, int n, double* out, cudaStream_t s) {

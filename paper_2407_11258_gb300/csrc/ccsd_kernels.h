@@ -14,7 +14,8 @@ int launch_assemble(const double* Rsym, const double* S, const double* Cp, const
                     double* t2n, double* err, double* part, int o, int v, cudaStream_t s);
 int launch_update_t1(const double* R1, const double* Fvo, const double* t1, const double* eps, double* t1n,
                      double* err, double* part, int o, int v, cudaStream_t s);
-int launch_energy(const double* t1, const double* t2, const double* ovov, double* part, int o, int v,
+// E = sum tau_ij^ab Lpair[i][j][a][b], Lpair = 2(ia|jb) - (ib|ja); returns the number of partials
+int launch_energy(const double* t1, const double* t2, const double* Lpair, double* part, int o, int v,
                   cudaStream_t s);
 void launch_finish_sum(const double* part, int n, double* out, cudaStream_t s);
 void launch_mp2_amps(const double* ovov, const double* eps, double* t2, int o, int v, cudaStream_t s);
