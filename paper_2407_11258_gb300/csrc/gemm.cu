@@ -52,16 +52,19 @@ __device__ __forceinline__ long long view_off(const View& v, long long r, int k)
   return view_roff(v, static_cast<int>(r)) + view_koff(v, k);
 }
 
+// Store scale * x: BF16 hi/lo planes (scale applied in FP32: the values keep ~16 bits anyway) or FP64.
 template <bool BF16>
-__device__ __forceinline__ void put(void* out, long long idx, long long plane, double x) {
+__device__ __forceinline__ void put(void* out, long long idx, long long plane, double x, double scale) {
   if (BF16) {
     __nv_bfloat16 hi, lo;
-    split_bf16(x, hi, lo);
+    const float xf = static_cast<float>(x) * static_cast<float>(scale);
+    hi = __float2bfloat16_rn(xf);
+    lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
     __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
     o[idx] = hi;
     o[idx + plane] = lo;
   } else {
-    static_cast<double*>(out)[idx] = x;
+    static_cast<double*>(out)[idx] = scale * x;
   }
 }
 
@@ -88,12 +91,12 @@ __global__ void k_pack(View v, void* out, int Kw, int ld, long long plane) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int k = ch * 256 + lane + 32 * t;
-      x[t] = (k < K && k < kend) ? v.scale * src[kflat ? static_cast<long long>(k) * v.sk0 : view_koff(v, k)] : 0.0;
+      x[t] = (k < K && k < kend) ? src[kflat ? static_cast<long long>(k) * v.sk0 : view_koff(v, k)] : 0.0;
     }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int k = ch * 256 + lane + 32 * t;
-      if (k < kend) put<BF16>(out, base + k, plane, x[t]);
+      if (k < kend) put<BF16>(out, base + k, plane, x[t], v.scale);
     }
   }
 }
@@ -117,7 +120,7 @@ __global__ void k_pack_t(View v, void* out, int Kw, int ld, long long plane) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = rb + tx, k = kb + ty + 8 * q;
-        x[q] = (r < rows && k < K) ? v.scale * v.src[view_off(v, r, k)] : 0.0;
+        x[q] = (r < rows && k < K) ? v.src[view_off(v, r, k)] : 0.0;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) tile[ty + 8 * q][tx] = x[q];
@@ -125,14 +128,14 @@ __global__ void k_pack_t(View v, void* out, int Kw, int ld, long long plane) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = rb + ty + 8 * q, k = kb + tx;
-        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ty + 8 * q]);
+        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ty + 8 * q], v.scale);
       }
       __syncthreads();
     } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = rb + ty + 8 * q, k = kb + tx;
-        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, 0.0);
+        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, 0.0, 1.0);
       }
     }
   }

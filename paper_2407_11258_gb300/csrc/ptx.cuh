@@ -169,10 +169,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 // BF16 split of an FP64 value: hi = bf16(x), lo = bf16(x - hi). hi*b_hi + hi*b_lo + lo*b_hi keeps
 // about 16 significant bits of every product (the lo*lo term, ~2^-16 relative, is dropped).
+// The residual is formed in FP32 from x rounded to FP32 (exact subtraction; the 2^-24 rounding of x
+// is far below the ~2^-16 the pair keeps): one FP64 conversion per element, no FP64 arithmetic, which
+// matters on a part whose FP64 pipe is a small fraction of its FP32 rate.
 __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   const float xf = static_cast<float>(x);
   hi = __float2bfloat16_rn(xf);
-  lo = __float2bfloat16_rn(static_cast<float>(x - static_cast<double>(__bfloat162float(hi))));
+  lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
 }
 
 }  // namespace lnocc
