@@ -356,10 +356,16 @@ __global__ void k_pair_L(const double* ovov, double* L, int o, int v) {
 // with its transpose, M[c][d] +- M[d][c]. One block per (al, b, 32 x 32 tile pair (cb <= db)): both tiles
 // are read coalesced into shared memory, and the packed rows (c fastest for fixed d, as tri_le(c, d)
 // runs) are written coalesced.
+__device__ __forceinline__ void split_bf16g(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) { split_bf16(x, hi, lo); }
+__device__ __forceinline__ void split_bf16g(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
 template <bool BF16, typename TG>
 __global__ void k_pack_vvvv(const TG* __restrict__ G, int a0, int v, void* Vp, void* Vm, int Kpp, int Kpm,
                             long long plane_p, long long plane_m) {
-  __shared__ double T1[32][33], T2[32][33];  // T1[c][d] = M[cb+c][db+d], T2[d][c] = M[db+d][cb+c]
+  __shared__ TG T1[32][33], T2[32][33];  // T1[c][d] = M[cb+c][db+d], T2[d][c] = M[db+d][cb+c]
   const int al = blockIdx.z, b = blockIdx.y, a = a0 + al;
   if (a > b) return;
   // tile pair index -> (cb, db) with cb <= db over T = ceil(v / 32) tiles
@@ -375,9 +381,9 @@ __global__ void k_pack_vvvv(const TG* __restrict__ G, int a0, int v, void* Vp, v
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   for (int r = ty; r < 32; r += 8) {
     const int c1 = cb + r, d1 = db + tx;
-    T1[r][tx] = (c1 < v && d1 < v) ? static_cast<double>(Mb[c1 * vv + d1]) : 0.0;
+    T1[r][tx] = (c1 < v && d1 < v) ? Mb[c1 * vv + d1] : TG(0);
     const int d2 = db + r, c2 = cb + tx;
-    T2[r][tx] = (d2 < v && c2 < v) ? static_cast<double>(Mb[d2 * vv + c2]) : 0.0;
+    T2[r][tx] = (d2 < v && c2 < v) ? Mb[d2 * vv + c2] : TG(0);
   }
   __syncthreads();
   const long long rowp = static_cast<long long>(tri_le(a, b)) * Kpp;
@@ -385,23 +391,24 @@ __global__ void k_pack_vvvv(const TG* __restrict__ G, int a0, int v, void* Vp, v
   for (int r = ty; r < 32; r += 8) {
     const int d = db + r, c = cb + tx;
     if (d >= v || c >= v || c > d) continue;
-    const double acbd = T1[tx][r], adbc = T2[r][tx];
-    const double xp = acbd + adbc;
+    // FP32 G (mixed path): sums and the BF16 split in FP32; FP64 G: FP64
+    const TG acbd = T1[tx][r], adbc = T2[r][tx];
+    const TG xp = acbd + adbc;
     const long long pp = rowp + tri_le(c, d);
     if (BF16) {
       __nv_bfloat16 hi, lo;
-      split_bf16(xp, hi, lo);
+      split_bf16g(xp, hi, lo);
       static_cast<__nv_bfloat16*>(Vp)[pp] = hi;
       static_cast<__nv_bfloat16*>(Vp)[pp + plane_p] = lo;
     } else {
       static_cast<double*>(Vp)[pp] = xp;
     }
     if (rowm >= 0 && c < d) {
-      const double xm = acbd - adbc;
+      const TG xm = acbd - adbc;
       const long long pm = rowm + tri_lt(c, d);
       if (BF16) {
         __nv_bfloat16 hi, lo;
-        split_bf16(xm, hi, lo);
+        split_bf16g(xm, hi, lo);
         static_cast<__nv_bfloat16*>(Vm)[pm] = hi;
         static_cast<__nv_bfloat16*>(Vm)[pm + plane_m] = lo;
       } else {

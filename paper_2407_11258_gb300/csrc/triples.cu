@@ -337,19 +337,24 @@ __global__ void k_t_finish(const double* part, long long nblk, double* out) {
   }
 }
 
-// dst row (y, a, i) <- src row (a, y, i) of a packed [planes][rows][Kp] operand (rows = v*v*o)
-template <typename T>
-__global__ void k_swap_outer_rows(const T* src, T* dst, int v, int o, int Kp, int planes) {
+// dst row (y, a, i) <- src row (a, y, i) of a packed [planes][rows][Kp] operand (rows = v*v*o): one
+// warp per row, 16-byte copies (a packed row is a multiple of 128 bytes)
+__global__ void k_swap_outer_rows(const uint4* __restrict__ src, uint4* __restrict__ dst, int v, int o, int nvec,
+                                  int planes) {
   const long long rows = 1LL * v * v * o;
-  const long long total = rows * Kp * planes;
-  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int k = idx % Kp;
-    const long long r = (idx / Kp) % rows;
-    const long long pl = idx / (Kp * rows);
-    const int i = r % o, a = (r / o) % v, y = r / (1LL * o * v);
+  const int lane = threadIdx.x % 32;
+  const long long nw = static_cast<long long>(gridDim.x) * blockDim.x / 32;
+  for (long long w = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) / 32; w < rows * planes;
+       w += nw) {
+    const long long r = w % rows, pl = w / rows;
+    const int i = static_cast<int>(r % o);
+    const long long q = r / o;
+    const int a = static_cast<int>(q % v);
+    const long long y = q / v;
     const long long sr = (1LL * a * v + y) * o + i;
-    dst[(pl * rows + r) * Kp + k] = src[(pl * rows + sr) * Kp + k];
+    const uint4* s = src + (pl * rows + sr) * nvec;
+    uint4* d = dst + (pl * rows + r) * nvec;
+    for (int e = lane; e < nvec; e += 32) d[e] = s[e];
   }
 }
 
@@ -436,15 +441,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       pack_cols(view(tmp, A_(nb, vv), A_(v, v), A_(o, nb * vv), kOne, kOne, A_(v, 1)), XT2, b0 * v * o, 0, v, s);
     }
     mixed = keep;
-    const long long tot = static_cast<long long>(XT2.rows) * XT2.Kp * (bf ? 2 : 1);
-    const int blocks = static_cast<int>(std::min<long long>((tot + 255) / 256, 152LL * 32));
+    const int planes = bf ? 2 : 1;
+    const int nvec = XT2.Kp * (bf ? 2 : 8) / 16;
+    const long long nrows = static_cast<long long>(XT2.rows) * planes;
+    const int blocks = static_cast<int>(std::min<long long>((nrows + 7) / 8, 152LL * 16));
     count_launch();
-    if (bf)
-      k_swap_outer_rows<unsigned short><<<blocks, 256, 0, s>>>(static_cast<const unsigned short*>(XT2.p),
-                                                                 static_cast<unsigned short*>(XT1.p), v, o, XT2.Kp, 2);
-    else
-      k_swap_outer_rows<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(XT2.p), static_cast<double*>(XT1.p),
-                                                       v, o, XT2.Kp, 1);
+    k_swap_outer_rows<<<blocks, 256, 0, s>>>(static_cast<const uint4*>(XT2.p), static_cast<uint4*>(XT1.p), v, o,
+                                             nvec, planes);
   }
   // l-parts (after the row swap, which copies whole rows): XT1[x][a][i][v + l] = -t_il^ax,
   // XT2[c][a][k][v + l] = -t_kl^ca (the l-terms enter W with a minus sign)
