@@ -137,6 +137,8 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
 // and every distinct ordering of (a, b, c); the i-sums are accumulated in Real and the block sum in FP64.
 // VFLY: only w is staged and v = w + disc s is recomputed where it is read (the slices, t1 columns and
 // d_m are in shared memory already); half the shared memory, for blocks too large to stage both.
+// Launched for the FP64 path and for the mixed path's VFLY blocks; the mixed path with both w and v
+// staged runs k_t_energy_f32 below.
 template <typename TW, typename Real, int NLO, bool VFLY>
 __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
                                   const double* __restrict__ eps, const double* __restrict__ t1,
@@ -284,6 +286,176 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
     for (int pi = 0; pi < 6; ++pi)
 #pragma unroll
       for (int al = 0; al < NLO; ++al) r_frag += zu[pi][al] * yu[pi][al];
+  }
+  double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
+  __shared__ double sh[2][32];
+  for (int off = 16; off > 0; off >>= 1) {
+    e_can += __shfl_xor_sync(0xffffffffu, e_can, off);
+    e_frag += __shfl_xor_sync(0xffffffffu, e_frag, off);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) {
+    sh[0][w] = e_can;
+    sh[1][w] = e_frag;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
+      s0 += sh[0][q];
+      s1 += sh[1][q];
+    }
+    out[2 * blk_id] = -s0 / 3.0;
+    out[2 * blk_id + 1] = -s1 / 3.0;
+  }
+}
+
+// Block energy of the mixed path with w and v both staged (FP32 W): the same quantities, orderings and
+// summation order as k_t_energy_staged<float, float, NLO, false>, with the data movement reworked:
+//  * the staging pass issues eight independent W loads per thread before it uses any of them;
+//  * w and v of one (y0, y1, y2) sit side by side, so a placement is one 8-byte shared-memory load;
+//  * the projected i-sums of z and y for one LO form a pair updated by one packed FP32 FMA, with
+//    U[i][alpha] duplicated into both halves of a pair in shared memory.
+template <int NLO>
+__global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ W, long long slot_stride, int b, int c0,
+                                                      int o, int v, const double* __restrict__ eps,
+                                                      const double* __restrict__ t1, const double* __restrict__ ovov,
+                                                      const double* __restrict__ U, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int slot = blockIdx.y, a = blockIdx.x;
+  const int c = c0 + slot;
+  const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
+  const int o2 = o * o, o3 = o2 * o;
+  const int S1 = o + 1, S0 = o * S1 + 1;  // padded strides of the staged block (odd for even o)
+  const int blk = o * S0;
+  float2* swv = reinterpret_cast<float2*>(smraw);  // (w, v) at y0 * S0 + y1 * S1 + y2
+  float* fs = reinterpret_cast<float*>(smraw) + 2 * blk;
+  const int P1 = o + 1, o2p = o * P1;
+  float* Sab = fs;  // (y0 a|y1 b)
+  float* Sac = Sab + o2p;
+  float* Sbc = Sac + o2p;
+  float* ta = Sbc + o2p;
+  float* tb = ta + o;
+  float* tc = tb + o;
+  float* dm = tc + o;
+  // U pairs (U[i][al], U[i][al]), 16-byte aligned for 128-bit loads
+  const int uoff = (2 * blk + 3 * o2p + 4 * o + 3) & ~3;
+  float* U2 = reinterpret_cast<float*>(smraw) + uoff;
+  const long long ov = 1LL * o * v;
+  const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
+  for (int idx = threadIdx.x; idx < o2; idx += blockDim.x) {
+    const int p = idx / o, q = idx % o;
+    Sab[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + b]);
+    Sac[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + c]);
+    Sbc[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + b) * ov + 1LL * q * v + c]);
+  }
+  for (int y = threadIdx.x; y < o; y += blockDim.x) {
+    ta[y] = static_cast<float>(t1[y * v + a]);
+    tb[y] = static_cast<float>(t1[y * v + b]);
+    tc[y] = static_cast<float>(t1[y * v + c]);
+    dm[y] = static_cast<float>(ex3 - eps[y]);
+  }
+  for (int idx = threadIdx.x; idx < o * NLO; idx += blockDim.x) {
+    const float u = static_cast<float>(U[idx]);
+    U2[2 * idx] = u;
+    U2[2 * idx + 1] = u;
+  }
+  __syncthreads();
+  const float* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
+  // W is stored [i][k][j] (j fastest) and read in that order; (y0, y2, y1) of idx advance by the
+  // fixed stride blockDim.x with carries
+  constexpr int kLoads = 8;
+  const int st = blockDim.x, d1 = st % o, d2 = (st / o) % o, d0 = st / o2;
+  int y1 = threadIdx.x % o, y2 = (threadIdx.x / o) % o, y0 = threadIdx.x / o2;
+  for (int base = threadIdx.x; base < o3; base += kLoads * st) {
+    float wr[kLoads];
+#pragma unroll
+    for (int u = 0; u < kLoads; ++u) wr[u] = base + u * st < o3 ? Wb[base + u * st] : 0.f;
+#pragma unroll
+    for (int u = 0; u < kLoads; ++u) {
+      if (base + u * st < o3) {
+        const float disc = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
+        const float sc = rsqrtf(dm[y0] + dm[y1] + dm[y2]);
+        swv[y0 * S0 + y1 * S1 + y2] = make_float2(wr[u] * sc, (wr[u] + disc) * sc);
+      }
+      y1 += d1;
+      int cy = y1 >= o;
+      y1 -= cy ? o : 0;
+      y2 += d2 + cy;
+      cy = y2 >= o;
+      y2 -= cy ? o : 0;
+      y0 += d0 + cy;
+    }
+  }
+  __syncthreads();
+  // placements and orderings as in k_t_energy_staged
+  constexpr int PM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int x0 = a, x1 = b, x2 = c;
+  auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
+  auto SS = [&](int p) { return p == 0 ? S0 : (p == 1 ? S1 : 1); };
+  bool act[6];
+#pragma unroll
+  for (int pi = 0; pi < 6; ++pi) {
+    bool dup = false;
+#pragma unroll
+    for (int q = 0; q < pi; ++q)
+      dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
+    act[pi] = !dup;
+  }
+  constexpr int NL = NLO > 0 ? NLO : 1;
+  float r_can = 0.f, r_frag = 0.f;
+  for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
+    const int j = jk / o, k = jk % o;
+    int off[6], si[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      off[q] = j * SS(PM[q][1]) + k * SS(PM[q][2]);
+      si[q] = SS(PM[q][0]);
+    }
+    float acc = 0.f;
+    float2 zy[6][NL];  // (sum_i U z, sum_i U y) per ordering and LO
+#pragma unroll
+    for (int pi = 0; pi < 6; ++pi)
+#pragma unroll
+      for (int al = 0; al < NL; ++al) zy[pi][al] = make_float2(0.f, 0.f);
+    for (int i = 0; i < o; ++i) {
+      float2 p[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        p[q] = swv[off[q]];
+        off[q] += si[q];
+      }
+      float2 u2[NL];
+      if constexpr (NLO == 1) {
+        u2[0] = reinterpret_cast<const float2*>(U2)[i];
+      } else if constexpr (NLO > 1) {
+#pragma unroll
+        for (int h = 0; h < NLO / 2; ++h) {
+          const float4 t = reinterpret_cast<const float4*>(U2)[i * (NLO / 2) + h];
+          u2[2 * h] = make_float2(t.x, t.y);
+          u2[2 * h + 1] = make_float2(t.z, t.w);
+        }
+      }
+#pragma unroll
+      for (int pi = 0; pi < 6; ++pi) {
+        if (!act[pi]) continue;
+        const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
+        auto idx = [&](int s0, int s1) {
+          return s0 == 0 ? (s1 == 1 ? 0 : 1) : (s0 == 1 ? (s1 == 0 ? 2 : 3) : (s1 == 0 ? 4 : 5));
+        };
+        const float z = 4 * p[idx(p0, p1)].x + p[idx(p1, p2)].x + p[idx(p2, p0)].x;
+        const float y = p[idx(p0, p1)].y - p[idx(p2, p1)].y;
+        acc += z * y;
+        const float2 zyv = make_float2(z, y);
+#pragma unroll
+        for (int al = 0; al < NLO; ++al) zy[pi][al] = __ffma2_rn(u2[al], zyv, zy[pi][al]);
+      }
+    }
+    r_can += acc;
+#pragma unroll
+    for (int pi = 0; pi < 6; ++pi)
+#pragma unroll
+      for (int al = 0; al < NLO; ++al) r_frag += zy[pi][al].x * zy[pi][al].y;
   }
   double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
   __shared__ double sh[2][32];
@@ -507,7 +679,8 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   cudaMemcpyAsync(dbat12, hbat12.data(), sizeof(BatchEntry) * hbat12.size(), cudaMemcpyHostToDevice, s);
 
   const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
-  const long long small_smem = (3LL * o * (o + 1) + 4LL * o + 8LL * o) * wsz;
+  // slices, t1 columns, d_m and U (up to 8 LOs, duplicated into pairs, plus 16-byte alignment)
+  const long long small_smem = (3LL * o * (o + 1) + 4LL * o + 16LL * o + 4) * wsz;
   const bool staged_full = 2LL * sblk * wsz + small_smem <= 200LL * 1024;
   const bool staged = (staged_full || sblk * wsz + small_smem <= 200LL * 1024) && nlo <= 8;
   // (the staged kernel reads U padded to its compile-time LO count)
@@ -528,33 +701,47 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   auto energy_launch = [&](const void* Wp, long long Sc, int b, int c0, int na, int nc, double* part) {
     dim3 grid(na, nc);
     count_launch();
-#define LN_E(T, R, K)                                                                                    \
+    // FP32 W with w and v staged: k_t_energy_f32; otherwise the generic staged kernel
+#define LN_F(K)                                                                                          \
   do {                                                                                                   \
     if (staged_full)                                                                                     \
-      k_t_energy_staged<T, R, K, false><<<grid, 256, esmem, s>>>(static_cast<const T*>(Wp), Sc, b, c0, o, v, \
-                                                                 eps, t1, ovov, dUp, nlo_t, part);       \
+      k_t_energy_f32<K><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps, t1,  \
+                                                 ovov, dUp, part);                                       \
     else                                                                                                 \
-      k_t_energy_staged<T, R, K, true><<<grid, 256, esmem, s>>>(static_cast<const T*>(Wp), Sc, b, c0, o, v,  \
-                                                                eps, t1, ovov, dUp, nlo_t, part);        \
+      k_t_energy_staged<float, float, K, true><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, \
+                                                                        c0, o, v, eps, t1, ovov, dUp,    \
+                                                                        nlo_t, part);                    \
+  } while (0)
+#define LN_D(K)                                                                                          \
+  do {                                                                                                   \
+    if (staged_full)                                                                                     \
+      k_t_energy_staged<double, double, K, false><<<grid, 256, esmem, s>>>(static_cast<const double*>(Wp), Sc, \
+                                                                           b, c0, o, v, eps, t1, ovov,   \
+                                                                           dUp, nlo_t, part);            \
+    else                                                                                                 \
+      k_t_energy_staged<double, double, K, true><<<grid, 256, esmem, s>>>(static_cast<const double*>(Wp), Sc, \
+                                                                          b, c0, o, v, eps, t1, ovov, dUp, \
+                                                                          nlo_t, part);                  \
   } while (0)
     if (bf) {
       switch (nlo_t) {
-        case 0: LN_E(float, float, 0); break;
-        case 1: LN_E(float, float, 1); break;
-        case 2: LN_E(float, float, 2); break;
-        case 4: LN_E(float, float, 4); break;
-        default: LN_E(float, float, 8); break;
+        case 0: LN_F(0); break;
+        case 1: LN_F(1); break;
+        case 2: LN_F(2); break;
+        case 4: LN_F(4); break;
+        default: LN_F(8); break;
       }
     } else {
       switch (nlo_t) {
-        case 0: LN_E(double, double, 0); break;
-        case 1: LN_E(double, double, 1); break;
-        case 2: LN_E(double, double, 2); break;
-        case 4: LN_E(double, double, 4); break;
-        default: LN_E(double, double, 8); break;
+        case 0: LN_D(0); break;
+        case 1: LN_D(1); break;
+        case 2: LN_D(2); break;
+        case 4: LN_D(4); break;
+        default: LN_D(8); break;
       }
     }
-#undef LN_E
+#undef LN_F
+#undef LN_D
   };
   if (staged) {
     // The attribute is per kernel and process-wide: set it once to the largest size the staged
@@ -565,11 +752,11 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       auto attr = [](const void* fn) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       };
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 0, false>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 1, false>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 2, false>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 4, false>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 8, false>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<1>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<2>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<4>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<8>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, false>));
