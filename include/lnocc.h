@@ -137,8 +137,12 @@ int lnocc_fragment_energy(lnocc_frag* f, int nlo, const double* U_frag, double* 
  *   nlo, U_frag [nocc][nlo] : fragment LO coefficients; U_frag == NULL (or nlo == 0) skips projection.
  *   e_t_full (host)         : canonical (T) energy, the trace of the (T) pair matrix (full active space).
  *   e_t_frag (host)         : sum_alpha sum_ii' U_i,alpha E_ii',(T) U_i',alpha (may be NULL).
- * FP64 precision: FP64 contractions. Mixed precision: W and V contractions as BF16x3/FP32 on tensor
- * cores, denominators, square roots, products and the energy sum in FP64.
+ * FP64 precision: FP64 contractions and energy arithmetic. Mixed precision: the W contractions as
+ * BF16x3/FP32 on tensor cores; the denominators' terms formed in FP64, the scaled w and v, their
+ * products and the i-sums in FP32, every block sum and the total in FP64.
+ * Allocates its temporaries per call (the packed (T) operands, a W chunk of at most 768 MB or one
+ * b-slab, the launch tables and the padded U) in the fragment's memory mode and frees them before it
+ * returns; LNOCC_ENOMEM when they do not fit. Synchronizes `stream`.
  */
 int lnocc_triples(lnocc_frag* f, int nlo, const double* U_frag, double* e_t_full, double* e_t_frag,
                   void* stream);
