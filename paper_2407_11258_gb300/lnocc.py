@@ -21,6 +21,7 @@ ERR_NAMES = {0: "LNOCC_OK", 1: "LNOCC_EINVAL", 2: "LNOCC_ENOMEM", 3: "LNOCC_ENOC
              5: "LNOCC_ETIMEOUT", 6: "LNOCC_ECUDA"}
 
 LNOCC_ORDER_LPT, LNOCC_ORDER_INPUT = 0, 1
+NFEAT = 8  # features per amplitude of the learned guess: X is [n][8]
 
 EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragment_energy", "lnocc_triples",
            "lnocc_debug_gemm", "lnocc_gemm_noalloc", "lnocc_frag_info", "lnocc_free_fragment", "lnocc_last_error",
@@ -145,6 +146,33 @@ def _ptr(x, dtype=None):
     return x.data_ptr()
 
 
+def _need(x, n, what):
+    """Reject an array argument whose element count differs from what the C entry point reads or
+    writes through its pointer (the kernels index by the declared sizes, so a shorter tensor would be
+    read or written past its end). None and raw integer pointers are passed through unchecked."""
+    if x is None or isinstance(x, int):
+        return
+    got = int(x.numel()) if hasattr(x, "numel") else int(x.size)
+    if got != int(n):
+        raise ValueError(f"{what}: expected {int(n)} elements, got {got}")
+
+
+def _rows(U, nocc, what="U_frag"):
+    """U_frag is [nocc][nlo]: two dimensions, nocc rows."""
+    if U is None or isinstance(U, int):
+        return
+    if U.dim() != 2 or int(U.shape[0]) != int(nocc):
+        raise ValueError(f"{what}: expected shape [{nocc}][nlo], got {tuple(U.shape)}")
+
+
+def _dims(frag):
+    """(nocc, nvir) of a fragment handle."""
+    if getattr(frag, "dims", None) is None:
+        inf = frag.info()
+        frag.dims = (inf.nocc, inf.nvir)
+    return frag.dims
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -169,8 +197,9 @@ def default_opts(**kw) -> Opts:
 class Fragment:
     """Owns an lnocc_frag handle; methods mirror the C entry points."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, dims=None):
         self.h = handle
+        self.dims = dims  # (nocc, nvir)
 
     def __del__(self):
         self.free()
@@ -187,16 +216,24 @@ class Fragment:
 
 
 def lnocc_build_ints(nocc, nvir, naux, eps, B, opts=None, stream=None) -> Fragment:
+    if nocc > 0 and nvir > 0 and naux > 0:  # (other sizes are rejected by the library itself)
+        n = nocc + nvir
+        _need(eps, n, "eps")
+        _need(B, naux * n * n, "B")
     h = ctypes.c_void_p()
     code = load().lnocc_build_ints(nocc, nvir, naux, _ptr(eps), _ptr(B), ctypes.byref(opts) if opts else None,
                                    _stream(stream), ctypes.byref(h))
     _check(code)
-    return Fragment(h)
+    return Fragment(h, (nocc, nvir))
 
 
 def lnocc_ccsd(frag: Fragment, t1_in=None, t2_in=None, guess_mode=LNOCC_GUESS_MP2, t1_out=None, t2_out=None,
                stream=None, allow_noconv=False):
     """Returns (e_corr, n_iter, status)."""
+    o, v = _dims(frag)
+    for x, n, what in ((t1_in, o * v, "t1_in"), (t2_in, o * o * v * v, "t2_in"), (t1_out, o * v, "t1_out"),
+                       (t2_out, o * o * v * v, "t2_out")):
+        _need(x, n, what)
     e = ctypes.c_double(0.0)
     it = ctypes.c_int(0)
     code = load().lnocc_ccsd(frag.h, _ptr(t1_in), _ptr(t2_in), guess_mode, _ptr(t1_out), _ptr(t2_out),
@@ -207,6 +244,7 @@ def lnocc_ccsd(frag: Fragment, t1_in=None, t2_in=None, guess_mode=LNOCC_GUESS_MP
 
 def lnocc_fragment_energy(frag: Fragment, U_frag, stream=None):
     """Returns (e_ccsd_frag, e_mp2_frag); U_frag is [nocc][nlo]."""
+    _rows(U_frag, _dims(frag)[0])
     ec, em = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(load().lnocc_fragment_energy(frag.h, int(U_frag.shape[1]), _ptr(U_frag), ctypes.byref(ec),
                                         ctypes.byref(em), _stream(stream)))
@@ -215,6 +253,7 @@ def lnocc_fragment_energy(frag: Fragment, U_frag, stream=None):
 
 def lnocc_triples(frag: Fragment, U_frag=None, stream=None):
     """Returns (e_t_full, e_t_frag)."""
+    _rows(U_frag, _dims(frag)[0])
     ef, eF = ctypes.c_double(0.0), ctypes.c_double(0.0)
     nlo = int(U_frag.shape[1]) if U_frag is not None else 0
     _check(load().lnocc_triples(frag.h, nlo, _ptr(U_frag), ctypes.byref(ef), ctypes.byref(eF), _stream(stream)))
@@ -225,6 +264,8 @@ def lnocc_debug_gemm(precision, A, B, C, stream=None):
     """C = A @ B.T through the contraction engine (diagnostic)."""
     M, K = A.shape
     N = B.shape[0]
+    _need(B, N * K, "B")
+    _need(C, M * N, "C")
     _check(load().lnocc_debug_gemm(precision, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
     return C
 
@@ -233,6 +274,8 @@ def lnocc_gemm_noalloc(precision, A, B, C, stream=None):
     """C = A @ B.T through the contraction engine using the library's fixed scratch (no device allocation)."""
     M, K = A.shape
     N = B.shape[0]
+    _need(B, N * K, "B")
+    _need(C, M * N, "C")
     _check(load().lnocc_gemm_noalloc(precision, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
     return C
 
@@ -250,6 +293,11 @@ def lnocc_solve_batch(frags, opts=None, bopts=None, stream=None, allow_noconv=Fa
     tensors as for lnocc_build_ints. Returns (status, [BatchResult per fragment])."""
     n = len(frags)
     items = (BatchItem * max(n, 1))()
+    for k, (o, v, q, eps, B, U) in enumerate(frags):  # every item checked before any pointer is taken
+        if o > 0 and v > 0 and q > 0:
+            _need(eps, o + v, f"item {k} eps")
+            _need(B, q * (o + v) ** 2, f"item {k} B")
+            _rows(U, o, f"item {k} U_frag")
     for k, (o, v, q, eps, B, U) in enumerate(frags):
         items[k] = BatchItem(o, v, q, int(U.shape[1]) if U is not None else 0, _ptr(eps), _ptr(B), _ptr(U))
     res = (BatchResult * max(n, 1))()
@@ -313,15 +361,20 @@ class Mlp:
     def set_norm(self, norm):
         import numpy as np
         nrm = np.ascontiguousarray(norm, dtype=np.float64)
+        _need(nrm, 17, "norm")
         _check(load().lnocc_mlp_set_norm(self.h, nrm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def fit_norm(self, X, dt, stream=None):
         import torch
+        _need(X, X.shape[0] * NFEAT, "X")
+        _need(dt, X.shape[0], "dt")
         _check(load().lnocc_mlp_fit_norm(self.h, X.shape[0], _ptr(X, torch.float32), _ptr(dt, torch.float32),
                                          _stream(stream)))
 
     def train_step(self, X, dt, lr, stream=None):
         import torch
+        _need(X, X.shape[0] * NFEAT, "X")
+        _need(dt, X.shape[0], "dt")
         loss = ctypes.c_double(0.0)
         _check(load().lnocc_mlp_train_step(self.h, X.shape[0], _ptr(X, torch.float32), _ptr(dt, torch.float32),
                                            lr, ctypes.byref(loss), _stream(stream)))
@@ -329,6 +382,7 @@ class Mlp:
 
     def forward(self, X, precision=LNOCC_PREC_FP64, stream=None):
         import torch
+        _need(X, X.shape[0] * NFEAT, "X")
         y = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
         _check(load().lnocc_mlp_forward(self.h, precision, X.shape[0], _ptr(X, torch.float32), _ptr(y),
                                         _stream(stream)))
@@ -336,6 +390,8 @@ class Mlp:
 
     def grad(self, X, dt, precision=LNOCC_PREC_FP64, stream=None):
         import torch
+        _need(X, X.shape[0] * NFEAT, "X")
+        _need(dt, X.shape[0], "dt")
         g = torch.empty(load().lnocc_mlp_nparams(), dtype=torch.float64, device=X.device)
         loss = ctypes.c_double(0.0)
         _check(load().lnocc_mlp_grad(self.h, precision, X.shape[0], _ptr(X, torch.float32), _ptr(dt, torch.float32),
@@ -346,11 +402,17 @@ class Mlp:
 def lnocc_mlp_samples(frag: Fragment, idx, X, dt=None, stream=None):
     """Features X [n][8] (float32) and targets dt [n] (float32) of flat amplitude indices idx (int64)."""
     import torch
+    n = idx.shape[0]
+    _need(idx, n, "idx")
+    _need(X, n * NFEAT, "X")
+    _need(dt, n, "dt")
     _check(load().lnocc_mlp_samples(frag.h, idx.shape[0], _ptr(idx, torch.int64), _ptr(X, torch.float32),
                                     _ptr(dt, torch.float32), _stream(stream)))
 
 
 def lnocc_mlp_guess(frag: Fragment, mlp: Mlp, t2_out, stream=None):
+    o, v = _dims(frag)
+    _need(t2_out, o * o * v * v, "t2_out")
     _check(load().lnocc_mlp_guess(frag.h, mlp.h, _ptr(t2_out), _stream(stream)))
     return t2_out
 

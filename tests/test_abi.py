@@ -116,3 +116,61 @@ def test_autotune_table_io_needs_no_gpu(lib, tmp_path):
             lnocc.lnocc_autotune_load(str(tmp_path / "missing.txt"))
     finally:
         lnocc.lnocc_autotune(prev)
+
+
+def test_binding_rejects_mis_sized_arrays_before_the_call(lib):
+    """The binding checks every array's element count against the sizes it passes, before the
+    pointer is taken: CPU tensors of the right size get as far as the CUDA-tensor check (TypeError),
+    mis-sized ones stop at the size check (ValueError). No device work in either case."""
+    import numpy as np
+    import torch
+    o, v, q = 2, 3, 4
+    n = o + v
+    eps, B = torch.zeros(n, dtype=torch.float64), torch.zeros(q, n, n, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        lnocc.lnocc_build_ints(o, v, q, eps, B)
+    with pytest.raises(ValueError, match="eps"):
+        lnocc.lnocc_build_ints(o, v, q, torch.zeros(n - 1, dtype=torch.float64), B)
+    with pytest.raises(ValueError, match="B"):
+        lnocc.lnocc_build_ints(o, v, q, eps, torch.zeros(q, n, n - 1, dtype=torch.float64))
+    f = lnocc.Fragment(None, (o, v))
+    t2 = torch.zeros(o, o, v, v, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        lnocc.lnocc_ccsd(f, t2_out=t2)
+    for kw in ({"t1_in": torch.zeros(o, v + 1, dtype=torch.float64)},
+               {"t2_in": torch.zeros(o, o, v, v - 1, dtype=torch.float64)},
+               {"t1_out": torch.zeros(o * v - 1, dtype=torch.float64)},
+               {"t2_out": torch.zeros(o, v, v, dtype=torch.float64)}):
+        with pytest.raises(ValueError, match=next(iter(kw))):
+            lnocc.lnocc_ccsd(f, **kw)
+    with pytest.raises(ValueError, match="t2_out"):
+        lnocc.lnocc_mlp_guess(f, None, torch.zeros(o, o, v, dtype=torch.float64))
+    U = torch.zeros(o, 1, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        lnocc.lnocc_triples(f, U)
+    for bad in (torch.zeros(o + 1, 1, dtype=torch.float64), torch.zeros(o, dtype=torch.float64)):
+        with pytest.raises(ValueError, match="U_frag"):
+            lnocc.lnocc_triples(f, bad)
+        with pytest.raises(ValueError, match="U_frag"):
+            lnocc.lnocc_fragment_energy(f, bad)
+    with pytest.raises(ValueError, match="item 0 B"):
+        lnocc.lnocc_solve_batch([(o, v, q, eps, torch.zeros(q, n, dtype=torch.float64), U)])
+    with pytest.raises(ValueError, match="item 1 U_frag"):
+        lnocc.lnocc_solve_batch([(o, v, q, eps, B, U), (o, v, q, eps, B, torch.zeros(o + 1, 1, dtype=torch.float64))])
+    A = torch.zeros(5, 7, dtype=torch.float64)
+    with pytest.raises(ValueError, match="C"):
+        lnocc.lnocc_debug_gemm(1, A, torch.zeros(3, 7, dtype=torch.float64), torch.zeros(5, 2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="B"):
+        lnocc.lnocc_gemm_noalloc(1, A, torch.zeros(3, 6, dtype=torch.float64), torch.zeros(5, 3, dtype=torch.float64))
+    idx = torch.zeros(6, dtype=torch.int64)
+    with pytest.raises(ValueError, match="X"):
+        lnocc.lnocc_mlp_samples(f, idx, torch.zeros(6, lnocc.NFEAT - 1, dtype=torch.float32))
+    with pytest.raises(ValueError, match="dt"):
+        lnocc.lnocc_mlp_samples(f, idx, torch.zeros(6, lnocc.NFEAT, dtype=torch.float32),
+                                torch.zeros(5, dtype=torch.float32))
+    m = lnocc.Mlp.__new__(lnocc.Mlp)  # no device handle: only the host-side checks run
+    m.h = None
+    with pytest.raises(ValueError, match="norm"):
+        m.set_norm(np.zeros(16))
+    with pytest.raises(ValueError, match="dt"):
+        m.train_step(torch.zeros(4, lnocc.NFEAT, dtype=torch.float32), torch.zeros(3, dtype=torch.float32), 1e-3)
