@@ -1,7 +1,8 @@
 """Write the stored oracle energies under tests/golden/ (calls only `oracle/` and the input generator).
 
     python tests/golden/make_golden.py small        # nocc=4/nvir=24, (T) at nocc=12/nvir=96, batch subset
-    python tests/golden/make_golden.py diamond      # nocc=16, nvir=240, naux=960 (tens of minutes)
+    python tests/golden/make_golden.py diamond      # nocc=16, nvir=240, naux=960, CCSD only (about 1.5 h)
+    python tests/golden/make_golden.py half         # nocc=16, nvir=120, naux=480 with (T) (about 30 min)
 
 Each file records the generator call that rebuilds the inputs, the oracle's
 energies (FP64) and its convergence data.
@@ -59,6 +60,14 @@ def main(tier):
         fr = synth.diamond_like()
         res = {"diamond_like": dict(gen="synth.diamond_like()", **solve(fr, with_t="--no-t" not in sys.argv, log=log))}
         path = os.path.join(HERE, "oracle_diamond.json")
+    elif tier == "half":
+        # the diamond-like generator at half the virtual space: (T) at the production nocc against the oracle
+        fr = synth.make_fragment(16, 120, 480, 2000, occ_range=(-1.2, -0.4), vir_range=(0.3, 4.0), decay=20.0,
+                                 frag=(0, 1))
+        gen = ("synth.make_fragment(16, 120, 480, 2000, occ_range=(-1.2, -0.4), vir_range=(0.3, 4.0), "
+               "decay=20.0, frag=(0, 1))")
+        res = {"half_diamond": dict(gen=gen, **solve(fr, log=log))}
+        path = os.path.join(HERE, "oracle_half_diamond.json")
     else:
         raise SystemExit(__doc__)
     res["_note"] = "written by tests/golden/make_golden.py from oracle/ only"

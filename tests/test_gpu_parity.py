@@ -141,6 +141,18 @@ def test_diamond_like_full_size(lnocc):
     assert_parity(got, ref, MIXED_TOL)
 
 
+def test_half_diamond_with_triples(lnocc):
+    """nocc=16 (the diamond-like occupied space), nvir=120, naux=480, 2 LOs: both paths against the
+    stored oracle energies with (T) included, which the full-size oracle cannot supply in reasonable
+    CPU time. Covers the (T) energy blocks at the production nocc against the oracle directly."""
+    ref = golden("oracle_half_diamond.json")["half_diamond"]
+    fr = synth.make_fragment(16, 120, 480, 2000, occ_range=(-1.2, -0.4), vir_range=(0.3, 4.0), decay=20.0,
+                             frag=(0, 1))
+    assert (fr.nocc, fr.nvir, fr.naux, fr.seed) == (ref["nocc"], ref["nvir"], ref["naux"], ref["seed"])
+    for prec, tol in ((1, MIXED_TOL), (0, FP64_TOL)):
+        assert_parity(gpu_solve(lnocc, fr, prec), ref, tol)
+
+
 # ------------------------------------------------------------------ properties
 
 def test_deterministic_repeat(lnocc):
