@@ -8,7 +8,8 @@ in for the paper's diamond fragment (seeded generator in paper_2407_11258_gb300/
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-fp64] [--no-cpu]
     python bench.py --workload batch [--nfrag 128] [--workers 0] [--autotune 1] [--steps 1] [--warmup 1]
     python bench.py --workload mlp [--ntrain 256] [--nheld 64] [--train-steps 2000] [--mlp-precision mixed]
-    python bench.py --workload triples      # nocc=32, nvir=480, naux=1600: one solve, (T) timed
+    python bench.py --workload triples      # nocc=32, nvir=480, naux=1600: one solve, (T) timed, plus the
+                                            # scaled fragment's error against the stored oracle energies
 
 Prints one JSON line (rank 0). `value` is model TFLOP/s of whole solves with inputs resident in HBM
 (inputs of 0.5 GB exceed the 129 MB L2, so no flush is needed between steps); `e2e` repeats the
@@ -289,7 +290,8 @@ def run_batch(args):
 
 
 def run_triples(args):
-    """(T)-dominated large fragment (nocc=32, nvir=480, naux=1600): one mixed solve, (T) timed."""
+    """(T)-dominated large fragment (nocc=32, nvir=480, naux=1600): one mixed solve, (T) timed; then the
+    mixed energies of the scaled fragment (nocc=12, nvir=96, naux=320) against the stored oracle."""
     import torch
     from paper_2407_11258_gb300 import build, lnocc, synth
     world, rank, local = dist_setup()
@@ -317,6 +319,17 @@ def run_triples(args):
     achieved = alg / (info.t_triples_gemm_ms * 1e-3) / 1e12
     if rank != 0:
         return
+    # error at the scaled size (nocc=12, nvir=96, naux=320) against the stored oracle energies, which
+    # tests/golden/make_golden.py wrote from the oracle (the full-size oracle (T) would take days)
+    ref = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_small.json")))["triples_scaled"]
+    frs = synth.triples_large(scaled=True)
+    eps_s, B_s, U_s = (torch.tensor(x, device="cuda") for x in (frs.eps, frs.B, frs.U_frag))
+    fs = lnocc.lnocc_build_ints(frs.nocc, frs.nvir, frs.naux, eps_s, B_s, opts)
+    es, _, _ = lnocc.lnocc_ccsd(fs, allow_noconv=True)
+    ets, etfs = lnocc.lnocc_triples(fs, U_s)
+    fs.free()
+    scaled = {"workload": "nocc=12 nvir=96 naux=320", "abs_err_vs_oracle": {
+        "e_ccsd": abs(es - ref["e_ccsd"]), "e_t": abs(ets - ref["e_t"]), "e_t_frag": abs(etfs - ref["e_t_frag"])}}
     print(json.dumps({
         "metric": METRIC, "value": trip / (info.t_triples_ms * 1e-3) / 1e12, "unit": "TFLOP/s ((T) model flops)",
         "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": info.t_triples_ms, "higher_is_better": True,
@@ -330,6 +343,7 @@ def run_triples(args):
                      "kernel": "k_gemm_tc ((T) W contractions)", "contraction_ms": info.t_triples_gemm_ms,
                      "note": f"useful 2o^3v^4+2o^4v^3 / contraction event time; peak = {peak_src} bf16 burst / 3"},
         "clocks": sampler.summary(),
+        "scaled_size": scaled,
     }), flush=True)
 
 
