@@ -144,7 +144,6 @@ void Frag::contract_packed_b(const View& a, const Packed& PB, int N, const OutMa
 // ------------------------------------------------------------------------------------------------
 int Frag::build(const double* eps_in, const double* B_in) {
   const long long n2 = 1LL * n * n, oo = 1LL * o * o, vv = 1LL * v * v, ov = 1LL * o * v;
-  const bool bf = mixed;
   eps = static_cast<double*>(alloc(n * 8));
   Boo = static_cast<double*>(alloc(N * oo * 8));
   Bov = static_cast<double*>(alloc(N * ov * 8));

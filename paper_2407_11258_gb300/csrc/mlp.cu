@@ -459,12 +459,6 @@ __global__ void __launch_bounds__(128) k_mlp_infer(int o, int v, const double* _
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
-__global__ void k_count_nonfinite(const double* __restrict__ x, long long n, int* __restrict__ flag) {
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
-       e += static_cast<long long>(gridDim.x) * blockDim.x)
-    if (!isfinite(x[e])) atomicExch(flag, 1);
-}
-
 int grid_of(long long n, int threads) {
   return static_cast<int>(std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, 152LL * 16)));
 }
