@@ -4,13 +4,13 @@
  * The operations follow Ye & Berkelbach, "Periodic Local Coupled-Cluster Theory for Insulators and
  * Metals" (arXiv 2407.11258):
  *   - the fragment Hamiltonian is given by its semi-canonical orbital energies (the diagonal of the
- *     fragment Fock matrix f^(F), Eq. 8) and density-fitted integrals (pq|rs) = sum_Q B_Qpq B_Qrs
- *     (Eq. 15a, Gamma-point real form);
- *   - CCSD is solved in the active space (Sec. II.B, Eq. 7);
+ *     fragment Fock matrix f^(F), Eq. 11) and density-fitted integrals (pq|rs) = sum_Q B_Qpq B_Qrs
+ *     (Eq. 27a, Gamma-point real form);
+ *   - CCSD is solved in the active space (Sec. II.B, Eq. 10-11);
  *   - correlation energies are projected onto the fragment's localized occupied orbitals: the CCSD
- *     pair matrix E_ii' (Eq. 7) and the (T) pair matrix E_ii',(T) (Eq. 10, intermediates of the
+ *     pair matrix E_ii' (Eq. 13) and the (T) pair matrix E_ii',(T) (Eq. 16, intermediates of the
  *     supplementary Sec. S1), contracted as E^(F) = sum_{alpha in F} sum_ii' U_i,alpha E_ii' U_i',alpha
- *     (Eq. 6 and Eq. 9).
+ *     (Eq. 12 and Eq. 15).
  *
  * Conventions for every entry point
  *   - Return value: LNOCC_OK (0) or one of the LNOCC_E* codes below; the message of the last failure on
@@ -42,7 +42,7 @@ extern "C" {
 #define LNOCC_PREC_FP64 0  /* every contraction in FP64 (plain GPU path) */
 #define LNOCC_PREC_MIXED 1 /* contractions as BF16x3 products with FP32 accumulation (tcgen05) */
 
-#define LNOCC_GUESS_MP2 0   /* t1 = 0, t2 = first-order amplitudes (Eq. 11, canonical form) */
+#define LNOCC_GUESS_MP2 0   /* t1 = 0, t2 = first-order amplitudes (Eq. 21, canonical form) */
 #define LNOCC_GUESS_GIVEN 1 /* start from t1_in / t2_in (restart / checkpoint resume) */
 #define LNOCC_GUESS_MLP 2   /* t1 = 0, t2 = learned guess of the model attached by lnocc_frag_set_mlp */
 
@@ -86,7 +86,7 @@ typedef struct lnocc_info {
 void lnocc_default_opts(lnocc_opts* opts);
 
 /*
- * lnocc_build_ints -- integral assembly for one fragment (Sec. II.D item 2, Eq. 15a at the Gamma point).
+ * lnocc_build_ints -- integral assembly for one fragment (Sec. II.D item 2, Eq. 27a at the Gamma point).
  *   nocc, nvir, naux : active occupied, virtual and auxiliary dimensions (nocc >= 1, nvir >= 1, naux >= 1).
  *   eps  [n]         : orbital energies (the fragment Fock diagonal); every virtual must lie above every
  *                      occupied (else LNOCC_ENUMERIC: the (T) denominators of Sec. S1 need -Delta > 0).
@@ -101,14 +101,14 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
                      void* stream, lnocc_frag** out);
 
 /*
- * lnocc_ccsd -- closed-shell CCSD amplitude equations in the fragment active space (Sec. II.B, Eq. 7;
+ * lnocc_ccsd -- closed-shell CCSD amplitude equations in the fragment active space (Sec. II.B, Eq. 10-11;
  * the paper solves canonical CCSD with H^(F); the spin-adapted equations are the T1-transformed
  * closed-shell form of Koch et al., Chem. Phys. Lett. 228, 233 (1994)).
  *   t1_in [o][v], t2_in [o][o][v][v] : starting amplitudes when guess_mode == LNOCC_GUESS_GIVEN, else
  *                                      ignored (may be NULL).
  *   t1_out, t2_out                    : optional (NULL allowed) copies of the converged amplitudes.
  *   e_corr (host)                     : E_c = sum_ijab tau_ij^ab [2(ia|jb) - (ib|ja)], tau = t2 + t1 t1
- *                                       (Eq. 5; the printed minus sign is read as +).
+ *                                       (Eq. 7; the printed minus sign is read as +).
  *   n_iter (host, may be NULL)        : iterations taken.
  * The converged amplitudes stay in the handle for lnocc_triples / lnocc_fragment_energy. The same
  * convergence test applies to every guess mode. Returns LNOCC_ENOCONV (with the last energy) when
@@ -121,7 +121,7 @@ int lnocc_ccsd(lnocc_frag* f, const double* t1_in, const double* t2_in, int gues
                double* t2_out, double* e_corr, int* n_iter, void* stream);
 
 /*
- * lnocc_fragment_energy -- projected CCSD and MP2 fragment energies (Eq. 6-7).
+ * lnocc_fragment_energy -- projected CCSD and MP2 fragment energies (Eq. 12-13).
  *   nlo, U_frag [nocc][nlo] : the fragment's LO coefficients in the occupied space (columns alpha in F).
  *   e_ccsd_frag (host)      : sum_alpha sum_ii' U_i,alpha E_ii' U_i',alpha with the CCSD pair matrix
  *                             E_ii' = sum_jab tau_ij^ab [2(i'a|jb) - (i'b|ja)] of the last lnocc_ccsd.
@@ -132,7 +132,7 @@ int lnocc_fragment_energy(lnocc_frag* f, int nlo, const double* U_frag, double* 
                           void* stream);
 
 /*
- * lnocc_triples -- LNO-(T) energy (Eq. 9-10 with the intermediates W, V, w, v of supplementary Sec. S1)
+ * lnocc_triples -- LNO-(T) energy (Eq. 15-16 with the intermediates W, V, w, v of supplementary Sec. S1)
  * from the amplitudes of the last lnocc_ccsd.
  *   nlo, U_frag [nocc][nlo] : fragment LO coefficients; U_frag == NULL (or nlo == 0) skips projection.
  *   e_t_full (host)         : canonical (T) energy, the trace of the (T) pair matrix (full active space).
@@ -255,7 +255,7 @@ int lnocc_autotune_stats(long long* entries, long long* hits, long long* misses,
 
 /* ------------------------------------------------------------------------------------------------
  * Learned T2 initial guess (no counterpart in the paper, whose CCSD starts from the MP2 amplitudes of
- * Eq. 11): t_ij^ab = t_ij^ab(MP2) + s_out g(x_ijab), g an MLP 8 -> 128 -> 128 -> 1 with SiLU on the
+ * Eq. 21): t_ij^ab = t_ij^ab(MP2) + s_out g(x_ijab), g an MLP 8 -> 128 -> 128 -> 1 with SiLU on the
  * standardised features x = [t_MP2, e_i, e_j, e_a, e_b, D_ij^ab, (ia|jb), (ib|ja)] of the canonical
  * member of {(i,j,a,b), (j,i,b,a)} (i < j, or i == j and a <= b). Training: mean squared error of g
  * against (t_converged - t_MP2) / s_out, Adam (beta1 0.9, beta2 0.999, eps 1e-8).

@@ -8,9 +8,9 @@ Local Coupled-Cluster Theory for Insulators and Metals" (arXiv 2407.11258) or
 the published formulation it follows.
 
 Modules
-  ccsd      closed-shell CCSD (T1-transformed form), MP2, energies      -- Sec. II.B, Eq. 5-7, Eq. 11
-  triples   LNO-(T) intermediates and the projected (T) energy          -- Eq. 9-10, SI Sec. S1
-  fragment  projection of an occupied-pair energy matrix onto LOs       -- Eq. 4, Eq. 6, Eq. 9
+  ccsd      closed-shell CCSD (T1-transformed form), MP2, energies      -- Sec. II.B, Eq. 7, 12-13, 21
+  triples   LNO-(T) intermediates and the projected (T) energy          -- Eq. 14-16, SI Sec. S1
+  fragment  projection of an occupied-pair energy matrix onto LOs       -- Eq. 7-8, Eq. 12, Eq. 15
   fci       brute-force two-electron FCI (pin for CCSD)
   spinorb   spin-orbital CCSD and (T) (independent pin for the closed-shell forms)
 """

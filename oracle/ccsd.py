@@ -1,7 +1,7 @@
 """ORACLE (test infrastructure only): closed-shell fragment CCSD in FP64 on the CPU.
 
 The paper does not print the CCSD amplitude equations; it solves canonical
-CCSD with the fragment Hamiltonian (Sec. II.B, Eq. 7). The equations here are
+CCSD with the fragment Hamiltonian (Sec. II.B, Eq. 10-11). The equations here are
 the closed-shell spin-adapted CCSD of the T1-transformed Hamiltonian as given
 by Koch, Christiansen, Kobayashi, Jorgensen and Helgaker, Chem. Phys. Lett.
 228, 233 (1994) and Helgaker, Jorgensen & Olsen, "Molecular
@@ -10,10 +10,10 @@ folded into the integrals, after which the doubles equations take the CCD-like
 form A2 + B2 + P(C2 + D2 + E2).
 
 Conventions (real orbitals, Sec. II):
-  * chemist's notation (pq|rs) = sum_Q B_Qpq B_Qrs (Eq. 15a at the Gamma point);
+  * chemist's notation (pq|rs) = sum_Q B_Qpq B_Qrs (Eq. 27a at the Gamma point);
   * occupied orbitals first; t1[i,a] = t_i^a; t2[i,j,a,b] = t_ij^ab, which is
     the paper's t_iajb (a pairs with i, b with j);
-  * tau = t2 + t1 t1 (Eq. 5 prints a minus sign; the plus sign is the one for
+  * tau = t2 + t1 t1 (Eq. 7 prints a minus sign; the plus sign is the one for
     which CCSD equals two-electron FCI, and tests pin it that way);
   * f is the fragment Fock matrix: its diagonal is the orbital energies; a
     full f with zero occupied-virtual block is accepted ("general Fock") so
@@ -31,7 +31,7 @@ def _f_matrix(eps_or_f, n):
 
 
 def core_hamiltonian(f, B, nocc):
-    """h_pq = f_pq - sum_k [2(pq|kk) - (pk|kq)]: the one-electron part whose HF Fock is f (Eq. 8)."""
+    """h_pq = f_pq - sum_k [2(pq|kk) - (pk|kq)]: the one-electron part whose HF Fock is f (Eq. 11)."""
     o = slice(0, nocc)
     J = np.einsum("Qpq,Qkk->pq", B, B[:, o, o])
     K = np.einsum("Qpk,Qkq->pq", B[:, :, o], B[:, o, :])
@@ -67,7 +67,7 @@ def t1_fock(h, Bh, t1, nocc):
 
 
 def mp2_amplitudes(eps, B, nocc):
-    """First-order doubles t_ij^ab = (ia|jb) / (e_i + e_j - e_a - e_b) (Eq. 11, canonical orbitals)."""
+    """First-order doubles t_ij^ab = (ia|jb) / (e_i + e_j - e_a - e_b) (Eq. 21, canonical orbitals)."""
     e = np.asarray(eps, dtype=np.float64)
     o, v = slice(0, nocc), slice(nocc, None)
     ovov = np.einsum("Qia,Qjb->iajb", B[:, o, v], B[:, o, v])
@@ -77,7 +77,7 @@ def mp2_amplitudes(eps, B, nocc):
 
 
 def pair_energy_matrix(t1, t2, B, nocc):
-    """Fragment pair matrix E_ii' = sum_jab tau_ij^ab [2(i'a|jb) - (i'b|ja)] (Eq. 5 and Eq. 7)."""
+    """Fragment pair matrix E_ii' = sum_jab tau_ij^ab [2(i'a|jb) - (i'b|ja)] (Eq. 9 and Eq. 13)."""
     o, v = slice(0, nocc), slice(nocc, None)
     ovov = np.einsum("Qia,Qjb->iajb", B[:, o, v], B[:, o, v])
     L = 2.0 * ovov - ovov.transpose(0, 3, 2, 1)          # L[i',a,j,b] = 2(i'a|jb) - (i'b|ja)
@@ -86,7 +86,7 @@ def pair_energy_matrix(t1, t2, B, nocc):
 
 
 def correlation_energy(t1, t2, B, nocc):
-    """E_c = sum_ijab tau_ij^ab [2(ia|jb) - (ib|ja)] (Eq. 5) = trace of the pair matrix."""
+    """E_c = sum_ijab tau_ij^ab [2(ia|jb) - (ib|ja)] (Eq. 7) = trace of the pair matrix."""
     return float(np.trace(pair_energy_matrix(t1, t2, B, nocc)))
 
 
@@ -183,7 +183,7 @@ def ccsd(eps_or_f, B, nocc, *, t1=None, t2=None, max_iter=200, tol_t=1e-10, tol_
          diis=True, diis_nvec=8, callback=None):
     """Solve the closed-shell CCSD equations by Jacobi updates t += Omega / D (optionally DIIS).
 
-    Starts from the MP2 amplitudes (Eq. 11) unless amplitudes are given.
+    Starts from the MP2 amplitudes (Eq. 21) unless amplitudes are given.
     Returns dict(e_corr, t1, t2, n_iter, converged, e_mp2, history).
     """
     n = B.shape[1]

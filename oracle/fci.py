@@ -2,10 +2,10 @@
 
 For two electrons (one doubly occupied orbital, nocc = 1) CCSD is exact, so
 E_CCSD = E_FCI - E_HF; this pins the whole closed-shell CCSD oracle,
-including the sign of the t1 t1 term in tau (Eq. 5).
+including the sign of the t1 t1 term in tau (Eq. 7).
 
 The singlet spatial wavefunction is Psi(r1, r2) = sum_pq C_pq phi_p(r1) phi_q(r2)
-with C symmetric and sum C_pq^2 = 1. With the Hamiltonian of Eq. 1 its energy is
+with C symmetric and sum C_pq^2 = 1. With the Hamiltonian of Eq. 2 its energy is
   E = sum C_pq C_rs [h_pr d_qs + d_pr h_qs + (pr|qs)],
 so E_FCI is the lowest eigenvalue of that operator on symmetric C.
 The one-electron part h is recovered from the Fock matrix of the closed-shell

@@ -1,9 +1,9 @@
 """ORACLE (test infrastructure only): projection of pair matrices onto fragment LOs.
 
-E^(F) = sum_{alpha in F} sum_ii' U_i,alpha E_ii' U_i',alpha (Eq. 6 for CCSD,
-Eq. 9 for (T)); with real orbitals the complex conjugate is dropped. When the
-columns of U span the occupied space (Eq. 3) the fragment energies of all
-fragments add up to the trace of E (Eq. 4).
+E^(F) = sum_{alpha in F} sum_ii' U_i,alpha E_ii' U_i',alpha (Eq. 12 for CCSD,
+Eq. 15 for (T)); with real orbitals the complex conjugate is dropped. When the
+columns of U span the occupied space (Eq. 5) the fragment energies of all
+fragments add up to the trace of E (Eq. 7).
 """
 from __future__ import annotations
 

@@ -1,6 +1,6 @@
 """ORACLE (test infrastructure only): the learned T2 initial guess in FP64 on the CPU.
 
-The paper starts every fragment's CCSD from first-order (MP2) amplitudes (Eq. 11, canonical form)
+The paper starts every fragment's CCSD from first-order (MP2) amplitudes (Eq. 21, canonical form)
 and has no learned component. The learned guess is a per-amplitude correction
     t_ij^ab(guess) = t_ij^ab(MP2) + s_out * g(x_ijab),
 where g is a small multilayer perceptron and x_ijab holds eight features of the amplitude:

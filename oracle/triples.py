@@ -1,7 +1,7 @@
 """ORACLE (test infrastructure only): LNO-(T) pair matrix in FP64 on the CPU.
 
 Follows the supplementary Sec. S1 (intermediates after Nagy & Kallay, J. Chem.
-Phys. 146, 214106 (2017)) and Eq. 10 of the main text:
+Phys. 146, 214106 (2017)) and Eq. 16 of the main text:
 
   W_ijk^abc = P_ijk^abc { sum_d (bd|ai) t_kj^cd - sum_l (ck|jl) t_il^ab }
   V_ijk^abc = W_ijk^abc + 1/2 P_ijk^abc { (ai|bj) t_k^c }
@@ -55,7 +55,7 @@ def V_block(i, j, k, W, t1, ovov):
 
 
 def pair_matrix(t1, t2, eps, B, nocc):
-    """(T) pair matrix E_ii',(T) (Eq. 10). Its trace is the canonical (T) energy."""
+    """(T) pair matrix E_ii',(T) (Eq. 16). Its trace is the canonical (T) energy."""
     e = np.asarray(eps, dtype=np.float64)
     if e.ndim == 2:
         e = np.diag(e)

@@ -2,7 +2,7 @@
 // the projected fragment energies (lnocc_fragment_energy).
 //
 // Equations: closed-shell CCSD in T1-transformed form (Koch et al., Chem. Phys. Lett. 228, 233
-// (1994)), with density-fitted integrals (pq|rs) = sum_Q B_Qpq B_Qrs (Eq. 15a, Gamma-point form).
+// (1994)), with density-fitted integrals (pq|rs) = sum_Q B_Qpq B_Qrs (Eq. 27a, Gamma-point form).
 // The T1 amplitudes are folded into the DF factors, B^ = (1 - T) B (1 + T); every dressed
 // integral block is then a contraction over Q. The particle-particle ladder is the exception: it
 // uses the undressed (ac|bd), assembled once in symmetric / antisymmetric packed form

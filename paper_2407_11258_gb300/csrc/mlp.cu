@@ -11,7 +11,7 @@
 // reductions; and the fused inference kernel that evaluates the guess for all o^2 v^2 amplitudes:
 // features and layer 1 on the CUDA cores, layer 2 as a 128 x 128 x 128 BF16 tcgen05 MMA per tile of
 // 128 amplitudes (operands in shared memory, FP32 accumulator in TMEM), layer 3 in the TMEM epilogue.
-// The paper has no learned component: its CCSD starts from MP2 amplitudes (Eq. 11).
+// The paper has no learned component: its CCSD starts from MP2 amplitudes (Eq. 21).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -1,5 +1,5 @@
 // LNO-(T): W and V intermediates of the supplementary Sec. S1 and the projected (T) pair energy of
-// Eq. 10, summed as E^(F) = sum_alpha sum_ii' U_i,alpha E_ii',(T) U_i',alpha (Eq. 9).
+// Eq. 16, summed as E^(F) = sum_alpha sum_ii' U_i,alpha E_ii',(T) U_i',alpha (Eq. 15).
 //
 // Loop structure ("virtual-outer"): for each pair b <= c and every a <= b the block
 // W^{abc}_{ijk} over all occupied (i,j,k) is formed. Because W and V are invariant under a

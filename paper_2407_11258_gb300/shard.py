@@ -1,6 +1,6 @@
 """Host-side sharding of independent fragments over ranks (no collective in the data path).
 
-Fragments are independent units (Sec. II.B: E_c = sum_F E^(F), Eq. 4 and Eq. 9), so a multi-GPU run
+Fragments are independent units (Sec. II.B: E_c = sum_F E^(F), Eq. 7 and Eq. 14), so a multi-GPU run
 assigns whole fragments to ranks and only the per-fragment energies are gathered at the end and
 summed in fragment order (deterministic regardless of the rank count).
 """

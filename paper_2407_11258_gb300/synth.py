@@ -9,12 +9,12 @@ inputs stand in for them with the shapes and value distributions of those
 fragments:
 
 * orbital energies: sorted uniform draws, occupied below virtual (the
-  semi-canonical fragment Fock diagonal, Eq. 8 and Eq. 11);
+  semi-canonical fragment Fock diagonal, Eq. 11 and Eq. 21);
 * B[Q,p,q]: real, symmetric in (p,q), entries N(0, 1/naux) scaled by
-  0.3*exp(-|p-q|/L) (the Gamma-point real form of the DF factors of Eq. 15a,
+  0.3*exp(-|p-q|/L) (the Gamma-point real form of the DF factors of Eq. 27a,
   (pq|rs) = sum_Q B_Qpq B_Qrs);
-* U: a random orthogonal occupied->LO rotation (Eq. 2, span-occupied
-  condition Eq. 3); a fragment is a subset of its columns.
+* U: a random orthogonal occupied->LO rotation (Eq. 3, span-occupied
+  condition Eq. 5); a fragment is a subset of its columns.
 
 Random numbers come from splitmix64 (Steele, Lea & Flood, OOPSLA 2014), a
 counter-based generator whose integer stream is identical on every platform;

@@ -2,7 +2,7 @@
 
 None of these compares the oracle with itself: each check uses an independent
 route (brute-force FCI, the spin-orbital formulation, explicit MP2 loops) or an
-exact identity (Eq. 3-4 sum rule, orbital-rotation invariance, perturbation
+exact identity (Eq. 5 and 7 sum rule, orbital-rotation invariance, perturbation
 orders, permutational symmetry).
 """
 import numpy as np
@@ -31,7 +31,7 @@ def test_ccsd_equals_fci_for_two_electrons(nvir, seed):
 
 
 def test_tau_sign_is_plus():
-    """Eq. 5 prints tau = t2 - t1 t1; only + t1 t1 reproduces FCI (planted minus sign must fail)."""
+    """Eq. 7 prints tau = t2 - t1 t1; only + t1 t1 reproduces FCI (planted minus sign must fail)."""
     fr = _frag(1, 9, 5, naux=40, scale=3.0)
     r = ccsd.ccsd(fr.eps, fr.B, 1, tol_t=1e-12, tol_e=1e-14)
     e_fci, e_hf = fci.fci_2e(fr.eps, fr.B)
@@ -146,7 +146,7 @@ def test_diis_does_not_move_the_fixed_point():
     assert abs(a["e_corr"] - b["e_corr"]) < 1e-10
 
 
-# ------------------------------------------------------------- projector (Eq. 3-9)
+# ------------------------------------------------------------- projector (Eq. 5-16)
 
 def test_fragment_energies_sum_to_total():
     fr = synth.single_fp64()
