@@ -11,7 +11,8 @@ Modules
   ccsd      closed-shell CCSD (T1-transformed form), MP2, energies      -- Sec. II.B, Eq. 7, 12-13, 21
   triples   LNO-(T) intermediates and the projected (T) energy          -- Eq. 14-16, SI Sec. S1
   fragment  projection of an occupied-pair energy matrix onto LOs       -- Eq. 7-8, Eq. 12, Eq. 15
+  mp2       full-system MP2 and the MP2 composite correction            -- Eq. 17, Eq. 12-13, Eq. 21
   fci       brute-force two-electron FCI (pin for CCSD)
   spinorb   spin-orbital CCSD and (T) (independent pin for the closed-shell forms)
 """
-from . import ccsd, triples, fragment, fci, spinorb  # noqa: F401
+from . import ccsd, triples, fragment, fci, spinorb, mp2  # noqa: F401
