@@ -47,3 +47,21 @@ def test_literal_generator_is_unphysical():
     ok = synth.single_fp64()
     e_ok = np.trace(ccsd.pair_energy_matrix(np.zeros((4, 24)), ccsd.mp2_amplitudes(ok.eps, ok.B, 4), ok.B, 4))
     assert -0.1 < e_ok < 0.0
+
+
+def test_device_generator_matches_the_cpu_streams_and_distribution():
+    """fragment_device (B drawn with torch's generator, here on the CPU device) takes eps and U from the
+    same splitmix64 streams as make_fragment, and draws B symmetric with the same entry variance
+    0.09 exp(-2|p-q|/20) / naux."""
+    torch = __import__("pytest").importorskip("torch")
+    for small in (False, True):
+        o, v, q, eps, B, U = synth.fragment_device(6, 30, 400, small, 77, "cpu", frag=(0, 2))
+        ref = synth.make_fragment(6, 30, 400, 77, small_gap=small, frag=(0, 2))
+        assert (o, v, q) == (6, 30, 400)
+        assert np.array_equal(eps.numpy(), ref.eps) and np.array_equal(U.numpy(), ref.U_frag)
+        b = B.numpy()
+        assert b.shape == (400, 36, 36) and np.array_equal(b, b.transpose(0, 2, 1))
+    p = np.arange(36)
+    w = np.exp(-2.0 * np.abs(p[:, None] - p[None, :]) / 20.0)
+    ratio = (b**2).mean(axis=0) * 400 / (0.09 * w)  # per (p,q): mean of 400 squared normals, ~1 +- 0.07
+    assert abs(ratio.mean() - 1.0) < 0.02 and 0.7 < ratio.min() and ratio.max() < 1.3
