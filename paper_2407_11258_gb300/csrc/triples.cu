@@ -311,7 +311,8 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
 }
 
 // Block energy of the mixed path with w and v both staged (FP32 W): the same quantities, orderings and
-// summation order as k_t_energy_staged<float, float, NLO, false>, with the data movement reworked:
+// summation order as k_t_energy_staged with Real = float and both w and v staged (the form it replaced
+// on this path), with the data movement reworked:
 //  * the staging pass issues eight independent W loads per thread before it uses any of them;
 //  * w and v of one (y0, y1, y2) sit side by side, so a placement is one 8-byte shared-memory load;
 //  * the projected i-sums of z and y for one LO form a pair updated by one packed FP32 FMA, with
