@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     hdr = open(os.path.join(ROOT, "include", "lnocc.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(lnocc_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(lnocc_[a-z0-9_]+)\s*\(", hdr)))
 
 
 @pytest.fixture(scope="module")
