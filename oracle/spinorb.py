@@ -148,3 +148,34 @@ def triples(t1, t2, fs, g, O):
     tc = Pijk(Pabc(x)) / D
     td = Pijk(Pabc(y)) / D
     return float(np.einsum("ijkabc,ijkabc->", tc * D, tc + td) / 36.0)
+
+
+def pair_energy_matrix(t1s, t2s, g, O):
+    """Occupied pair matrix of the spin-orbital CCSD energy, summed over spin to spatial indices.
+
+    The spin-orbital correlation energy 1/4 sum_IJAB <IJ||AB> tau_IJ^AB (Stanton et al. 1991, f_ov = 0)
+    is split by the occupied index I of tau and the index I' that replaces it on the integral:
+    E_II' = 1/4 sum_JAB <I'J||AB> tau_IJ^AB, tau_IJ^AB = t_IJ^AB + t_I^A t_J^B - t_I^B t_J^A. Spin
+    orbitals 2p (alpha) and 2p+1 (beta) belong to spatial orbital p; the returned spatial matrix sums
+    both spins of i and of i'. Its trace is the spin-orbital CCSD energy. This is an independent route
+    (antisymmetrised spin-orbital integrals) to the closed-shell pair matrix of Eq. 9 and Eq. 13.
+    """
+    o, v = slice(0, O), slice(O, g.shape[0])
+    tau = t2s + np.einsum("ia,jb->ijab", t1s, t1s) - np.einsum("ib,ja->ijab", t1s, t1s)
+    E = 0.25 * np.einsum("kjab,ijab->ik", g[o, o, v, v], tau)
+    return E[0::2, 0::2] + E[0::2, 1::2] + E[1::2, 0::2] + E[1::2, 1::2]
+
+
+def to_spin_amplitudes(t1, t2):
+    """Closed-shell t1[i,a], t2[i,j,a,b] = t_ij^ab to spin-orbital t1s, antisymmetric t2s (spin orbital
+    2p + s for spatial p, spin s): t_IJ^AB = t_ij^ab d(s_I,s_A) d(s_J,s_B) - t_ij^ba d(s_I,s_B) d(s_J,s_A)."""
+    o, v = t1.shape
+    t1s = np.zeros((2 * o, 2 * v))
+    t2s = np.zeros((2 * o, 2 * o, 2 * v, 2 * v))
+    for s in range(2):
+        t1s[s::2, s::2] = t1
+    for si in range(2):
+        for sj in range(2):
+            t2s[si::2, sj::2, si::2, sj::2] += t2
+            t2s[si::2, sj::2, sj::2, si::2] -= t2.transpose(0, 1, 3, 2)
+    return t1s, t2s
