@@ -40,9 +40,15 @@ namespace {
 // Position permutations of three slots, listed as (p1, p2, p3) in 0-based slots.
 __constant__ int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
-// Block energy. One CTA per (pair, a) with a <= b; threads over (j, k).
-// W: [slot][a][i][j][k]; out: per block {canonical, projected} partials (FP64).
-__global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
+// Block energy, generic form: one CTA per (pair, a) with a <= b; threads over (j, k). Any nocc and any
+// number of LOs: the projected i-sums are kept for up to kLoChunk LOs at a time, and for more LOs the
+// i loop is repeated per chunk (the canonical part is accumulated in the first pass only). W is FP64
+// (plain path) or FP32 (mixed path); the arithmetic here is FP64 on both.
+// W: [slot][a][i][k][j]; out: per block {canonical, projected} partials (FP64).
+constexpr int kLoChunk = 8;
+
+template <typename TW>
+__global__ void k_t_energy(const TW* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
                            const double* __restrict__ eps, const double* __restrict__ t1,
                            const double* __restrict__ ovov, const double* __restrict__ U, int nlo,
                            double* __restrict__ out) {
@@ -51,14 +57,14 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
   const int c = c0 + slot;
   const long long oblk = 1LL * o * o * o;
   const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
-  const double* Wb = W + slot * slot_stride + a * oblk;
+  const TW* Wb = W + slot * slot_stride + a * oblk;
   const int x[3] = {a, b, c};
   const double ex = eps[o + a] + eps[o + b] + eps[o + c];
   const long long ov = 1LL * o * v;
   auto widx = [&](int y0, int y1, int y2) { return (1LL * y0 * o + y2) * o + y1; };  // W stored [a][i][k][j]
   // w and v of the block at occupied (y0, y1, y2)
   auto wv = [&](int y0, int y1, int y2, double& w, double& vv) {
-    const double Wv = Wb[widx(y0, y1, y2)];
+    const double Wv = static_cast<double>(Wb[widx(y0, y1, y2)]);
     const double Vv = Wv + ovov[(1LL * y0 * v + a) * ov + 1LL * y1 * v + b] * t1[y2 * v + c] +
                       ovov[(1LL * y0 * v + a) * ov + 1LL * y2 * v + c] * t1[y1 * v + b] +
                       ovov[(1LL * y1 * v + b) * ov + 1LL * y2 * v + c] * t1[y0 * v + a];
@@ -67,6 +73,7 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
     vv = Vv * s;
   };
   double e_can = 0.0, e_frag = 0.0;
+  const int nchunk = nlo > 0 ? (nlo + kLoChunk - 1) / kLoChunk : 1;
   for (int jk = threadIdx.x; jk < o * o; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
     for (int pi = 0; pi < 6; ++pi) {
@@ -77,33 +84,38 @@ __global__ void k_t_energy(const double* __restrict__ W, long long slot_stride, 
         dup = x[kPerm[q][0]] == x[p0] && x[kPerm[q][1]] == x[p1] && x[kPerm[q][2]] == x[p2];
       if (dup) continue;
       // ordering T = (x[p0], x[p1], x[p2]); W^T_{ijk} = W^{abc}_y with y[p0]=i, y[p1]=j, y[p2]=k
-      double zs[32], ys[32];
-      for (int i = 0; i < o; ++i) {
-        int y[3];
-        double w0, w1, w2, v0, v3, dummy;
-        y[p0] = i; y[p1] = j; y[p2] = k;        // T
-        wv(y[0], y[1], y[2], w0, v0);
-        y[p1] = i; y[p2] = j; y[p0] = k;        // T o c   = (t2, t3, t1): slots (p1, p2, p0)
-        wv(y[0], y[1], y[2], w1, dummy);
-        y[p2] = i; y[p0] = j; y[p1] = k;        // T o c^2 = (t3, t1, t2): slots (p2, p0, p1)
-        wv(y[0], y[1], y[2], w2, dummy);
-        y[p2] = i; y[p1] = j; y[p0] = k;        // (t3, t2, t1): slots (p2, p1, p0)
-        wv(y[0], y[1], y[2], dummy, v3);
-        const double z = 4.0 * w0 + w1 + w2;
-        const double yy = v0 - v3;
-        e_can += z * yy;
-        if (i < 32) {
-          zs[i] = z;
-          ys[i] = yy;
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int al0 = ch * kLoChunk;
+        const int nal = nlo > 0 ? min(kLoChunk, nlo - al0) : 0;
+        double zu[kLoChunk], yu[kLoChunk];
+#pragma unroll
+        for (int q = 0; q < kLoChunk; ++q) zu[q] = yu[q] = 0.0;
+        for (int i = 0; i < o; ++i) {
+          int y[3];
+          double w0, w1, w2, v0, v3, dummy;
+          y[p0] = i; y[p1] = j; y[p2] = k;        // T
+          wv(y[0], y[1], y[2], w0, v0);
+          y[p1] = i; y[p2] = j; y[p0] = k;        // T o c   = (t2, t3, t1): slots (p1, p2, p0)
+          wv(y[0], y[1], y[2], w1, dummy);
+          y[p2] = i; y[p0] = j; y[p1] = k;        // T o c^2 = (t3, t1, t2): slots (p2, p0, p1)
+          wv(y[0], y[1], y[2], w2, dummy);
+          y[p2] = i; y[p1] = j; y[p0] = k;        // (t3, t2, t1): slots (p2, p1, p0)
+          wv(y[0], y[1], y[2], dummy, v3);
+          const double z = 4.0 * w0 + w1 + w2;
+          const double yy = v0 - v3;
+          if (ch == 0) e_can += z * yy;
+#pragma unroll
+          for (int q = 0; q < kLoChunk; ++q) {
+            if (q < nal) {
+              const double u = U[i * nlo + al0 + q];
+              zu[q] += u * z;
+              yu[q] += u * yy;
+            }
+          }
         }
-      }
-      for (int al = 0; al < nlo; ++al) {
-        double zu = 0.0, yu = 0.0;
-        for (int i = 0; i < o && i < 32; ++i) {
-          zu += U[i * nlo + al] * zs[i];
-          yu += U[i * nlo + al] * ys[i];
-        }
-        e_frag += zu * yu;
+#pragma unroll
+        for (int q = 0; q < kLoChunk; ++q)
+          if (q < nal) e_frag += zu[q] * yu[q];
       }
     }
   }
@@ -687,9 +699,10 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   // (the staged kernel reads U padded to its compile-time LO count)
   const size_t esmem = (staged_full ? 2 : 1) * sblk * wsz + static_cast<size_t>(small_smem);
   // the energy kernel is compiled for 0, 1, 2, 4 or 8 LOs; U is zero-padded to the next size
+  // (the generic kernel, used when the staged ones are not, reads U as given: any nlo)
   const int nlo_t = nlo == 0 ? 0 : nlo <= 1 ? 1 : nlo <= 2 ? 2 : nlo <= 4 ? 4 : 8;
   double* dUp = nullptr;
-  if (nlo_t > 0) {
+  if (staged && nlo_t > 0) {
     dUp = static_cast<double*>(tmp_alloc(static_cast<size_t>(o) * nlo_t * 8));
     if (!dUp) {
       cleanup();
@@ -774,10 +787,6 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 4, true>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 8, true>));
     });
-  } else if (bf) {
-    cleanup();
-    set_error("lnocc_triples: nocc too large for the staged (T) energy kernel in this build");
-    return LNOCC_EINVAL;
   }
   auto omap = [&](double beta) {
     OutMap m{bf ? nullptr : static_cast<double*>(W), 0, 0, 0, 0, 1 << 30, 1 << 30, 1.0, beta};
@@ -842,8 +851,12 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       energy_launch(W, Sc, b, c0, na, nc, tpart + 2 * ch.part);
     } else {
       count_launch();
-      k_t_energy<<<dim3(na, nc), 128, 0, s>>>(static_cast<const double*>(W), Sc, b, c0, o, v, eps, t1, ovov, dU, nlo,
-                                              tpart + 2 * ch.part);
+      if (bf)
+        k_t_energy<float><<<dim3(na, nc), 128, 0, s>>>(static_cast<const float*>(W), Sc, b, c0, o, v, eps, t1, ovov,
+                                                       dU, nlo, tpart + 2 * ch.part);
+      else
+        k_t_energy<double><<<dim3(na, nc), 128, 0, s>>>(static_cast<const double*>(W), Sc, b, c0, o, v, eps, t1,
+                                                        ovov, dU, nlo, tpart + 2 * ch.part);
     }
   }
   k_t_finish<<<1, 1024, 0, s>>>(tpart, nblk_total, scal + 4);
