@@ -164,7 +164,11 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
  *   the process exits; the packed operands need (M + N) * roundup(K, 64) * (8 bytes FP64 | 4 bytes mixed)
  *   plus 256 bytes, and larger requests return LNOCC_EINVAL before any device work.
  *   The first call on a device looks up that array's device address (cudaGetSymbolAddress, with the device
- *   current); make that first call before any stream capture.
+ *   current); make that first call before any stream capture. With CUDA's default lazy module loading the
+ *   array is only placed in device memory at that first call, so make it before another allocator claims
+ *   the free memory (from then on the array stays put).
+ *   The tile autotuner only looks its table up here: in mode 2 (lnocc_autotune) a table miss falls back
+ *   to the fixed rule instead of timing candidates, which would allocate and synchronize.
  *   All calls share the array and it keeps the last call's contents: calls that overlap on the GPU (other
  *   streams, other host threads) race on it. The call synchronizes `stream` before it returns.
  *   Device pointers, row-major FP64; precision LNOCC_PREC_FP64 or LNOCC_PREC_MIXED.

@@ -965,6 +965,11 @@ void out_extent(const OutMap& C, int M, int N, long long* lo, long long* hi) {
 }
 }  // namespace
 
+bool& autotune_timing_allowed() {
+  static thread_local bool allowed = true;
+  return allowed;
+}
+
 int autotune_mode(int mode) {
   const int prev = tuner().mode.load();
   if (mode >= 0) tuner().mode.store(mode);
@@ -1073,7 +1078,7 @@ static void dispatch_tc(const Packed& A0, const Packed& B0, const Packed* A1, co
       }
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (!found && mode == 2 && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+    if (!found && mode == 2 && autotune_timing_allowed() && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       bn = tune_bn(A0, B0, A1, B1, a, gridM, s, bn);
       std::lock_guard<std::mutex> lk(T.mu);
       T.table[key] = bn;

@@ -127,6 +127,10 @@ inline void count_launch(long long n = 1) {
 // on a miss); 2: time the candidates for shapes missing from the table (synchronous; not while the
 // stream is being captured). autotune_mode(-1) only reads the mode.
 int autotune_mode(int mode);
+// Per host thread: false keeps the tuner from timing candidates on this thread (mode 2 then acts as
+// mode 1). Timing allocates a scratch output and synchronizes, which callers that must not allocate
+// or synchronize cannot allow.
+bool& autotune_timing_allowed();
 void autotune_stats(long long out[4]);  // entries, hits, misses, shapes tuned
 bool autotune_save(const char* path);
 bool autotune_load(const char* path);

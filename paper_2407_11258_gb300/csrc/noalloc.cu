@@ -79,10 +79,14 @@ extern "C" int lnocc_gemm_noalloc(int precision, int M, int N, int K, const doub
   const Ax one{1, 0};
   pack(view(A, one, one, Ax{M, K}, one, one, Ax{K, 1}), PA, s);
   pack(view(B, one, one, Ax{N, K}, one, one, Ax{K, 1}), PB, s);
-  // no split-K here: its partials would need workspace of their own
+  // no split-K here: its partials would need workspace of their own; and no tile timing by the
+  // autotuner (its mode 2 allocates a scratch output and synchronizes): table lookups only
   const SplitWs saved = split_ws();
   split_ws() = SplitWs{};
+  const bool timing = autotune_timing_allowed();
+  autotune_timing_allowed() = false;
   gemm(PA, PB, M, N, K, out_rowmajor(C, N), s, dstatus);
+  autotune_timing_allowed() = timing;
   split_ws() = saved;
   int st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -48,3 +48,33 @@ def test_noalloc_rejects_oversized_requests(lnocc):
         lnocc.lnocc_gemm_noalloc(0, A, B, C)
     assert ei.value.code == lnocc.LNOCC_EINVAL
     assert "32 MiB" in str(ei.value)
+
+
+@pytest.mark.gpu
+def test_noalloc_never_times_tiles_in_tuning_mode(lnocc):
+    """With the library-wide tuner in mode 2, a table miss on an ordinary contraction times the tile
+    candidates (which allocates a scratch output and synchronizes). The allocation-free entry point must
+    only look the table up: no shape tuned, no device memory taken, the same result as before."""
+    g = torch.Generator(device="cpu").manual_seed(99)
+    M, N, K = 333, 97, 517  # a shape bucket no other test tunes
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(N, K, generator=g, dtype=torch.float64).cuda()
+    C = torch.empty(M, N, dtype=torch.float64, device="cuda")
+    C_ref = torch.empty(M, N, dtype=torch.float64, device="cuda")
+    lnocc.lnocc_gemm_noalloc(1, A, B, C_ref)  # first call on the device: symbol lookup, module load
+    torch.cuda.synchronize()
+    prev = lnocc.lnocc_autotune(2)
+    try:
+        before = lnocc.lnocc_autotune_stats()
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(2):
+            lnocc.lnocc_gemm_noalloc(1, A, B, C)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        after = lnocc.lnocc_autotune_stats()
+    finally:
+        lnocc.lnocc_autotune(prev)
+    assert after["tuned"] == before["tuned"]
+    assert after["misses"] >= before["misses"] + 2  # the lookups did happen
+    assert free1 == free0
+    assert torch.equal(C, C_ref)
