@@ -22,7 +22,11 @@
  *   - Orbital order: occupied first (nocc), then virtual (nvir); n = nocc + nvir.
  *   - Amplitudes: t1[i][a] = t_i^a (nocc x nvir); t2[i][j][a][b] = t_ij^ab (nocc^2 x nvir^2), which is
  *     the paper's t_iajb (virtual a pairs with occupied i, b with j); t_ij^ab = t_ji^ba.
- *   - The library allocates device memory only inside lnocc_build_ints (held by the handle).
+ *   - Device memory is allocated by lnocc_build_ints (held by the handle until lnocc_free_fragment).
+ *     lnocc_ccsd and lnocc_fragment_energy allocate nothing. lnocc_triples needs temporaries of
+ *     lnocc_workspace_bytes(...) bytes: from a workspace the caller attached with lnocc_frag_set_workspace
+ *     (then it allocates nothing), else it allocates and frees them itself within the call. The other
+ *     allocating calls say so (the diagnostic GEMM, the batch runtime, MLP handles, autotuner mode 2).
  */
 #ifndef LNOCC_H
 #define LNOCC_H
@@ -62,7 +66,9 @@ typedef struct lnocc_opts {
   int verbose;        /* 1: print one line per iteration to stderr */
   int graph;          /* 1 (default): after the first iteration, replay each CCSD iteration from a CUDA
                          graph captured once per fragment (same kernels, same results; fewer host launches) */
-  int reserved[5];
+  int triples_chunk_mb; /* bound on the W chunk of lnocc_triples in MB (0, the default: 768); part of the
+                           workspace size that lnocc_workspace_bytes reports */
+  int reserved[4];
 } lnocc_opts;
 
 typedef struct lnocc_info {
@@ -80,6 +86,7 @@ typedef struct lnocc_info {
   long long kernel_launches; /* library-wide count of kernel launches so far (monotonic) */
   double t_triples_gemm_ms;  /* last lnocc_triples: device time of its contraction launches (CUDA events) */
   double t_triples_ms;       /* last lnocc_triples: device time of the whole call (CUDA events) */
+  long long device_allocs;   /* library-wide count of device allocations made so far (monotonic) */
 } lnocc_info;
 
 /* Fill `opts` with the defaults listed above (precision = LNOCC_PREC_MIXED). */
@@ -140,12 +147,31 @@ int lnocc_fragment_energy(lnocc_frag* f, int nlo, const double* U_frag, double* 
  * FP64 precision: FP64 contractions and energy arithmetic. Mixed precision: the W contractions as
  * BF16x3/FP32 on tensor cores; the denominators' terms formed in FP64, the scaled w and v, their
  * products and the i-sums in FP32, every block sum and the total in FP64.
- * Allocates its temporaries per call (the packed (T) operands, a W chunk of at most 768 MB or one
- * b-slab, the launch tables and the padded U) in the fragment's memory mode and frees them before it
- * returns; LNOCC_ENOMEM when they do not fit. Synchronizes `stream`.
+ * Any nocc and any number of LOs (up to 8 LOs and while a block of the (T) energy fits shared memory the
+ * staged energy kernels run; otherwise a generic kernel that stages nothing).
+ * Temporaries (the packed (T) operands, a W chunk of at most opts.triples_chunk_mb or one b-slab, the
+ * per-block partial sums, the launch tables and the padded U) come from the attached workspace
+ * (lnocc_frag_set_workspace; LNOCC_EINVAL if it is smaller than lnocc_workspace_bytes), or else are
+ * allocated in the fragment's memory mode and freed before the call returns (LNOCC_ENOMEM when they do
+ * not fit). Synchronizes `stream`.
  */
 int lnocc_triples(lnocc_frag* f, int nlo, const double* U_frag, double* e_t_full, double* e_t_frag,
                   void* stream);
+
+/*
+ * lnocc_workspace_bytes -- device scratch that lnocc_triples needs for a fragment of these sizes
+ * (Sec. II.D's (T) step: packed W/V operands, the W chunk and the block partial sums), for the precision
+ * and opts->triples_chunk_mb of `opts` (NULL: defaults). *bytes receives the size.
+ */
+int lnocc_workspace_bytes(int nocc, int nvir, int naux, const lnocc_opts* opts, long long* bytes);
+
+/*
+ * lnocc_frag_set_workspace -- attach caller-owned device memory (at least lnocc_workspace_bytes bytes for
+ * the fragment's sizes and options, else LNOCC_EINVAL) from which lnocc_triples takes its temporaries, so
+ * that no call after lnocc_build_ints allocates. The caller keeps ownership; the memory must stay valid
+ * while attached and must not be used by other work during lnocc_triples. NULL detaches.
+ */
+int lnocc_frag_set_workspace(lnocc_frag* f, void* workspace, long long workspace_bytes);
 
 /*
  * lnocc_debug_gemm -- diagnostic: C[M][N] = A[M][K] B[N][K]^T through the library's contraction engine
@@ -154,6 +180,16 @@ int lnocc_triples(lnocc_frag* f, int nlo, const double* U_frag, double* e_t_full
  * lets the contraction kernels be checked on their own.
  */
 int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const double* B, double* C, void* stream);
+
+/*
+ * lnocc_debug_wait -- diagnostic of the bounded device wait that every mbarrier wait in the library uses:
+ * a one-thread kernel waits for the first phase of an mbarrier with a wall-clock budget of budget_ns
+ * (0 .. 2e9 ns; the library's own waits use 2 s). arrive != 0 arrives first (the wait succeeds: LNOCC_OK);
+ * arrive == 0 lets nothing arrive, the budget runs out and the call returns LNOCC_ETIMEOUT with the context
+ * intact. *waited_ns (host, may be NULL) receives the time the kernel spent waiting. Not part of the
+ * method (the paper has no device code); allocates 16 bytes and synchronizes `stream`.
+ */
+int lnocc_debug_wait(int arrive, long long budget_ns, long long* waited_ns, void* stream);
 
 /*
  * lnocc_gemm_noalloc -- C[M][N] = A[M][K] B[N][K]^T like lnocc_debug_gemm, but without allocating device
@@ -174,6 +210,25 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
  *   Device pointers, row-major FP64; precision LNOCC_PREC_FP64 or LNOCC_PREC_MIXED.
  */
 int lnocc_gemm_noalloc(int precision, int M, int N, int K, const double* A, const double* B, double* C, void* stream);
+
+/*
+ * lnocc_mp2_energy -- canonical closed-shell MP2 correlation energy of the whole system, the first term of
+ * the MP2 composite correction (Eq. 17): Delta E_c,MP2 = E_c,MP2 - sum_F E_c,MP2^(F), whose fragment terms
+ * are the e_mp2_frag of lnocc_fragment_energy (Eq. 12-13 with the first-order amplitudes of Eq. 21).
+ *   E_c,MP2 = sum_ijab (ia|jb) [2 (ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b), (ia|jb) = sum_Q B_Qia B_Qjb.
+ *   precision          : LNOCC_PREC_FP64 (FP64 contraction) or LNOCC_PREC_MIXED ((ia|jb) as BF16x3 products
+ *                        with FP32 accumulation); denominators, products and sums in FP64 on both.
+ *   nocc, nvir, naux   : the system's occupied, virtual and auxiliary dimensions (nocc * nvir <= 2^30).
+ *   eps [nocc + nvir]  : canonical orbital energies (device), occupied first; every virtual above every occupied.
+ *   B_ov [naux][nocc][nvir] : the occupied-virtual block of the DF factors (device).
+ *   workspace, workspace_bytes : caller-owned device scratch of at least lnocc_mp2_workspace_bytes(...) bytes,
+ *                        or NULL (the call then allocates and frees its own); LNOCC_EINVAL when too small.
+ *   e_mp2 (host)       : the energy (Eh).
+ * The sum over blocks is taken in a fixed order (repeatable bit for bit). Synchronizes `stream`.
+ */
+int lnocc_mp2_workspace_bytes(int precision, int nocc, int nvir, int naux, long long* bytes);
+int lnocc_mp2_energy(int precision, int nocc, int nvir, int naux, const double* eps, const double* B_ov,
+                     void* workspace, long long workspace_bytes, double* e_mp2, void* stream);
 
 /* ------------------------------------------------------------------------------------------------
  * Batched fragments.

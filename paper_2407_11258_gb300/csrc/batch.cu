@@ -50,7 +50,8 @@ long long kp(long long k) { return (std::max(k, 1LL) + 63) / 64 * 64; }
 
 // Device bytes of one fragment handle at its peak (build transients and the (T) operands included),
 // from the allocation plan of Frag::build / build_consts / triples.
-long long estimate_fragment_bytes(int o_, int v_, int N_, bool mixed, int n_refine, int diis, bool do_t) {
+long long estimate_fragment_bytes(int o_, int v_, int N_, bool mixed, int n_refine, int diis, bool do_t,
+                                  int chunk_mb) {
   const long long o = o_, v = v_, N = N_, n = o + v, oo = o * o, vv = v * v, ov = o * v;
   const long long L = ov + oo * vv;
   const long long np_o = o * (o + 1) / 2, nm_o = std::max(1LL, o * (o - 1) / 2);
@@ -60,9 +61,7 @@ long long estimate_fragment_bytes(int o_, int v_, int N_, bool mixed, int n_refi
   b += 8 * (3 * L + 8 * oo * vv + 2 * oo * ov + 2 * oo * oo + N * ov + ov + vv + 2 * oo);
   b += 8 * (np_v * np_o + nm_v * nm_o + N * ov);
   b += 8 * 2 * std::min(diis, 8) * L;
-  long long cap = std::max({N * o * kp(v), N * v * kp(v), N * v * kp(o), n * kp(n), v * kp(N * o), vv * kp(N),
-                            ov * kp(N), N * kp(ov), ov * kp(ov), v * kp(N * v), v * kp(oo * v), oo * kp(vv),
-                            oo * v * kp(o), vv * kp(oo), oo * v * kp(v), o * vv * kp(o)});
+  const long long cap = packing_scratch_elems(o_, v_, N_);
   b += 2 * 8 * cap + 8 * (1LL << 22);
   auto consts = [&](long long esz) {
     long long c = np_o * kp(np_v) + nm_o * kp(nm_v) + (2 * ov + oo + vv) * kp(N) + oo * kp(vv) + 2 * ov * kp(ov) +
@@ -75,16 +74,7 @@ long long estimate_fragment_bytes(int o_, int v_, int N_, bool mixed, int n_refi
   };
   b += consts(mixed ? 4 : 8);
   if (mixed && n_refine > 0) b += consts(8);
-  if (do_t) {
-    const long long esz = mixed ? 4 : 8;
-    long long t = esz * (2 * vv * o * kp(v) + 2 * v * oo * kp(v) + 2 * vv * o * kp(o) + 2 * v * oo * kp(o) +
-                         vv * kp(N));
-    t += 8 * (oo * ov + std::max(1LL, std::min(v, (1LL << 26) / (o * vv))) * o * vv);
-    long long max_slab = 0;
-    for (long long bb = 0; bb < v; ++bb) max_slab = std::max(max_slab, (bb + 1) * (v - bb) * oo * o);
-    t += std::max(std::min(768LL << 20, esz * max_slab), esz * v * oo * o) + 16 * v * v * v;
-    b += t;
-  }
+  if (do_t) b += static_cast<long long>(triples_plan(o_, v_, N_, mixed, chunk_mb).total);
   return b + b / 16 + (64LL << 20);
 }
 
@@ -171,7 +161,8 @@ int lnocc_solve_batch(int nfrag, const lnocc_batch_item* items, const lnocc_opts
                         (bo.triples ? triples_flops(it.nocc, it.nvir) : 0.0) +
                         2.0 * it.naux * (it.nocc + it.nvir) * double(it.nvir) * it.nvir * it.nvir;
     const long long bytes =
-        estimate_fragment_bytes(it.nocc, it.nvir, it.naux, mixed, o.n_refine, o.diis_space, bo.triples != 0);
+        estimate_fragment_bytes(it.nocc, it.nvir, it.naux, mixed, o.n_refine, o.diis_space, bo.triples != 0,
+                                o.triples_chunk_mb);
     sh.pending.push_back(Job{f, cost, bytes});
   }
   if (bo.order == LNOCC_ORDER_LPT)

@@ -48,7 +48,8 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
   lnocc_default_opts(&o);
   if (opts) o = *opts;
   if ((o.precision != LNOCC_PREC_FP64 && o.precision != LNOCC_PREC_MIXED) || o.max_iter < 0 || o.diis_space < 0 ||
-      o.diis_space > 8 || o.n_refine < 0 || (o.graph != 0 && o.graph != 1) || !(o.conv_rms > 0) || !(o.conv_energy > 0)) {
+      o.diis_space > 8 || o.n_refine < 0 || (o.graph != 0 && o.graph != 1) || !(o.conv_rms > 0) || !(o.conv_energy > 0) ||
+      o.triples_chunk_mb < 0) {
     lnocc::set_error("lnocc_build_ints: bad options");
     return LNOCC_EINVAL;
   }
@@ -123,6 +124,41 @@ int lnocc_triples(lnocc_frag* h, int nlo, const double* U_frag, double* e_t_full
   return h->f.triples(U_frag ? nlo : 0, U_frag, e_t_full, e_t_frag);
 }
 
+int lnocc_workspace_bytes(int nocc, int nvir, int naux, const lnocc_opts* opts, long long* bytes) {
+  lnocc::set_error("");
+  lnocc_opts o;
+  lnocc_default_opts(&o);
+  if (opts) o = *opts;
+  if (!bytes || nocc < 1 || nvir < 1 || naux < 1 || o.triples_chunk_mb < 0 ||
+      (o.precision != LNOCC_PREC_FP64 && o.precision != LNOCC_PREC_MIXED)) {
+    lnocc::set_error("lnocc_workspace_bytes: bad arguments");
+    return LNOCC_EINVAL;
+  }
+  *bytes = static_cast<long long>(
+      lnocc::triples_plan(nocc, nvir, naux, o.precision == LNOCC_PREC_MIXED, o.triples_chunk_mb).total);
+  return LNOCC_OK;
+}
+
+int lnocc_frag_set_workspace(lnocc_frag* h, void* workspace, long long workspace_bytes) {
+  lnocc::set_error("");
+  if (!h) {
+    lnocc::set_error("lnocc_frag_set_workspace: bad arguments");
+    return LNOCC_EINVAL;
+  }
+  Frag& f = h->f;
+  if (workspace) {
+    const size_t need = lnocc::triples_plan(f.o, f.v, f.N, f.mixed, f.opts.triples_chunk_mb).total;
+    if (workspace_bytes < 0 || static_cast<size_t>(workspace_bytes) < need) {
+      lnocc::set_error("lnocc_frag_set_workspace: workspace smaller than lnocc_workspace_bytes (" +
+                       std::to_string(need) + " bytes)");
+      return LNOCC_EINVAL;
+    }
+  }
+  f.ws_ext = workspace;
+  f.ws_ext_bytes = workspace ? static_cast<size_t>(workspace_bytes) : 0;
+  return LNOCC_OK;
+}
+
 int lnocc_frag_info(const lnocc_frag* h, lnocc_info* info) {
   if (!h || !info) return LNOCC_EINVAL;
   const Frag& f = h->f;
@@ -144,6 +180,7 @@ int lnocc_frag_info(const lnocc_frag* h, lnocc_info* info) {
   info->kernel_launches = lnocc::launch_counter().load();
   info->t_triples_gemm_ms = f.t_gemm_ms;
   info->t_triples_ms = f.t_triples_ms;
+  info->device_allocs = lnocc::alloc_counter().load();
   return LNOCC_OK;
 }
 
@@ -156,6 +193,7 @@ int lnocc_debug_gemm(int precision, int M, int N, int K, const double* A, const 
   PA.bf16 = PB.bf16 = bf;
   const int Kp = lnocc::round_up(K, 64);
   int* dstatus = nullptr;
+  lnocc::count_alloc(4);
   LN_CUDA(cudaMalloc(&PA.p, static_cast<size_t>(M) * Kp * (bf ? 4 : 8)));
   LN_CUDA(cudaMalloc(&PB.p, static_cast<size_t>(N) * Kp * (bf ? 4 : 8)));
   LN_CUDA(cudaMalloc(&dstatus, 16));

@@ -32,6 +32,7 @@ static inline Ax A(int n, long long s) { return Ax{n, s}; }
 void* Frag::dev_alloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 256;
+  count_alloc();
   const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -142,6 +143,39 @@ void Frag::contract_packed_b(const View& a, const Packed& PB, int N, const OutMa
 // ------------------------------------------------------------------------------------------------
 // Integral assembly
 // ------------------------------------------------------------------------------------------------
+// Elements of each packing scratch buffer: the largest packed operand (rows x K rounded up to 64) of any
+// contraction that goes through Frag::contract / contract_packed_b, for either ordering of nocc and nvir.
+long long packing_scratch_elems(int o_, int v_, int N_) {
+  const long long o = o_, v = v_, N = N_, n = o + v, oo = o * o, vv = v * v, ov = o * v;
+  auto Kp = [](long long k) { return static_cast<long long>(round_up(static_cast<int>(std::max(k, 1LL)), 64)); };
+  long long cap = 0;
+  cap = std::max(cap, 1LL * N * o * Kp(v));
+  cap = std::max(cap, 1LL * N * v * Kp(v));
+  cap = std::max(cap, 1LL * N * v * Kp(o));
+  cap = std::max(cap, 1LL * n * Kp(n));
+  cap = std::max(cap, 1LL * v * Kp(1LL * N * o));
+  cap = std::max(cap, 1LL * vv * Kp(N));
+  cap = std::max(cap, 1LL * ov * Kp(N));
+  cap = std::max(cap, 1LL * N * Kp(ov));
+  cap = std::max(cap, 1LL * ov * Kp(ov));
+  cap = std::max(cap, 1LL * v * Kp(1LL * N * v));
+  cap = std::max(cap, 1LL * v * Kp(oo * v));
+  cap = std::max(cap, 1LL * oo * Kp(vv));
+  cap = std::max(cap, 1LL * oo * v * Kp(o));
+  cap = std::max(cap, 1LL * vv * Kp(oo));
+  cap = std::max(cap, 1LL * oo * v * Kp(v));
+  cap = std::max(cap, 1LL * o * vv * Kp(o));
+  // operands whose size grows with nocc (the largest when nocc > nvir)
+  cap = std::max(cap, 1LL * N * o * Kp(o));   // B^_oo rows (Q, k), K i
+  cap = std::max(cap, 1LL * n * Kp(1LL * N * o));  // core Hamiltonian exchange, rows p, K (Q, k)
+  cap = std::max(cap, 1LL * oo * Kp(oo));     // hole-hole ladder W_kl^ij
+  cap = std::max(cap, 1LL * o * Kp(1LL * N * v));  // B_ov rows i, K (Q, a); Mtmp
+  cap = std::max(cap, 1LL * o * Kp(oo * v));  // g^_kilc rows i, K (k, l, c)
+  cap = std::max(cap, 1LL * oo * Kp(N));      // (T): B_oo rows (j, l), K Q
+  cap = std::max(cap, 1LL * oo * v * Kp(o));
+  return cap;
+}
+
 int Frag::build(const double* eps_in, const double* B_in) {
   const long long n2 = 1LL * n * n, oo = 1LL * o * o, vv = 1LL * v * v, ov = 1LL * o * v;
   eps = static_cast<double*>(alloc(n * 8));
@@ -207,25 +241,7 @@ int Frag::build(const double* eps_in, const double* B_in) {
     h_scal = nullptr;
     oom = true;
   }
-  // scratch for packed operands: the largest operand of any contraction (see the list in DESIGN)
-  auto Kp = [](long long k) { return static_cast<long long>(round_up(static_cast<int>(std::max(k, 1LL)), 64)); };
-  long long cap = 0;
-  cap = std::max(cap, 1LL * N * o * Kp(v));
-  cap = std::max(cap, 1LL * N * v * Kp(v));
-  cap = std::max(cap, 1LL * N * v * Kp(o));
-  cap = std::max(cap, 1LL * n * Kp(n));
-  cap = std::max(cap, 1LL * v * Kp(1LL * N * o));
-  cap = std::max(cap, 1LL * vv * Kp(N));
-  cap = std::max(cap, 1LL * ov * Kp(N));
-  cap = std::max(cap, 1LL * N * Kp(ov));
-  cap = std::max(cap, 1LL * ov * Kp(ov));
-  cap = std::max(cap, 1LL * v * Kp(1LL * N * v));
-  cap = std::max(cap, 1LL * v * Kp(oo * v));
-  cap = std::max(cap, 1LL * oo * Kp(vv));
-  cap = std::max(cap, 1LL * oo * v * Kp(o));
-  cap = std::max(cap, 1LL * vv * Kp(oo));
-  cap = std::max(cap, 1LL * oo * v * Kp(v));
-  cap = std::max(cap, 1LL * o * vv * Kp(o));
+  const long long cap = packing_scratch_elems(o, v, N);
   scr_bytes = static_cast<size_t>(cap) * 8;
   scrA = alloc(scr_bytes);
   scrB = alloc(scr_bytes);

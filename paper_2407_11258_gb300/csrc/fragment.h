@@ -29,6 +29,16 @@ struct Consts {
   bool built = false;
 };
 
+// Sizes (bytes) of the device temporaries of one lnocc_triples call (triples.cu).
+struct TriplesPlan {
+  size_t xt, to, ovoo, pbvv, ovvv_chunk, w, tpart, batch, u, total;
+  long long welems, nblk;
+  int bc;
+};
+TriplesPlan triples_plan(int o, int v, int N, bool bf, int chunk_mb);
+// Elements (FP64-sized) of each of the two packing scratch buffers of a fragment (ccsd.cu).
+long long packing_scratch_elems(int o, int v, int N);
+
 struct Frag {
   int o = 0, v = 0, N = 0, n = 0;
   lnocc_opts opts{};
@@ -44,6 +54,8 @@ struct Frag {
   bool scratch_overflow = false;
   cudaMemPool_t pool = nullptr;
   double* h_ext = nullptr;  // caller-owned pinned host buffer (16 doubles) used instead of cudaMallocHost
+  void* ws_ext = nullptr;  // caller-owned workspace for the (T) temporaries (lnocc_frag_set_workspace)
+  size_t ws_ext_bytes = 0;
   void* alloc(size_t bytes, bool zero = false);
   void* dev_alloc(size_t bytes);  // raw allocation in the fragment's memory mode (not tracked)
   void dev_free(void* p);

@@ -30,6 +30,10 @@ std::atomic<long long>& launch_counter() {
   static std::atomic<long long> n{0};
   return n;
 }
+std::atomic<long long>& alloc_counter() {
+  static std::atomic<long long> n{0};
+  return n;
+}
 long long& thread_launch_counter() {
   static thread_local long long n = 0;
   return n;
@@ -1020,6 +1024,7 @@ static int tune_bn(const Packed& A0, const Packed& B0, const Packed* A1, const P
   if (lo < 0 || hi < lo) return fallback;
   const size_t esz = a.C.dst32 ? 4 : 8;
   void* scratch = nullptr;
+  count_alloc();
   if (cudaMalloc(&scratch, static_cast<size_t>(hi + 1) * esz) != cudaSuccess) {
     cudaGetLastError();
     return fallback;

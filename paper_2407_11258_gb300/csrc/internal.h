@@ -118,6 +118,9 @@ GemmStats& gemm_stats();  // per host thread
 // calling thread's own count (used to count the kernels a captured CUDA graph holds).
 std::atomic<long long>& launch_counter();
 long long& thread_launch_counter();
+// Library-wide count of device allocations made by the library (monotonic, all threads).
+std::atomic<long long>& alloc_counter();
+inline void count_alloc(long long n = 1) { alloc_counter().fetch_add(n, std::memory_order_relaxed); }
 inline void count_launch(long long n = 1) {
   launch_counter().fetch_add(n, std::memory_order_relaxed);
   thread_launch_counter() += n;

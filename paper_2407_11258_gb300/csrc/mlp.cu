@@ -564,6 +564,7 @@ int ensure_ws(Mlp& m, size_t bytes) {
   if (m.ws) cudaFree(m.ws);
   m.ws = nullptr;
   m.ws_bytes = 0;
+  count_alloc();
   if (cudaMalloc(&m.ws, bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("lnocc_mlp: device allocation failed (workspace)");
@@ -617,6 +618,7 @@ int lnocc_mlp_create(const float* params, lnocc_mlp** out) {
   if (!h) return LNOCC_ENOMEM;
   Mlp& m = h->m;
   const size_t pb = sizeof(float) * lnocc::kNParams;
+  lnocc::count_alloc(6);
   if (cudaMalloc(&m.p, pb) != cudaSuccess || cudaMalloc(&m.m, pb) != cudaSuccess ||
       cudaMalloc(&m.v, pb) != cudaSuccess || cudaMalloc(&m.norm, 17 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&m.gbuf, sizeof(double) * lnocc::kNParams) != cudaSuccess ||

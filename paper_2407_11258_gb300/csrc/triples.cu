@@ -23,8 +23,8 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdlib>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "ccsd_kernels.h"
@@ -545,6 +545,39 @@ __global__ void k_swap_outer_rows(const uint4* __restrict__ src, uint4* __restri
 
 }  // namespace
 
+// Device temporaries of one lnocc_triples call, in allocation order. Every size here is what the call
+// asks for; with a caller workspace attached the call carves them from it in this order (256-byte
+// aligned), so lnocc_workspace_bytes and the call agree by construction.
+TriplesPlan triples_plan(int o, int v, int N, bool bf, int chunk_mb) {
+  TriplesPlan p{};
+  const long long oo = 1LL * o * o, vv = 1LL * v * v, ooo = oo * o;
+  const size_t esz = bf ? 4 : 8;
+  auto packed = [&](long long rows, int K) { return static_cast<size_t>(rows) * round_up(std::max(K, 1), 64) * esz; };
+  const int Kt = v + o;
+  p.xt = packed(vv * o, Kt);
+  p.to = packed(v * oo, Kt);
+  p.ovoo = static_cast<size_t>(ooo * v * 8);
+  p.pbvv = packed(vv, N);
+  p.bc = static_cast<int>(std::max(1LL, std::min<long long>(v, (1LL << 26) / (o * vv))));
+  p.ovvv_chunk = static_cast<size_t>(p.bc) * o * vv * 8;
+  // W chunk: up to chunk_mb (fewer, larger contraction launches measured faster than chunks that fit
+  // L2), but never more than the largest slab (b + 1)(v - b) o^3 needs, and at least one c of a slab
+  long long max_slab = 0;
+  for (int bb = 0; bb < v; ++bb) max_slab = std::max(max_slab, 1LL * (bb + 1) * (v - bb) * ooo);
+  const long long cmb = chunk_mb > 0 ? chunk_mb : 768;
+  p.welems = std::max<long long>(std::min<long long>((cmb << 20) / static_cast<long long>(esz), max_slab), v * ooo);
+  p.w = static_cast<size_t>(p.welems) * esz;
+  p.nblk = 0;
+  for (int b = 0; b < v; ++b) p.nblk += 1LL * (b + 1) * (v - b);
+  p.tpart = static_cast<size_t>(p.nblk) * 2 * 8;
+  p.batch = sizeof(BatchEntry) * static_cast<size_t>(std::max(1LL, vv / 2 + v));  // one entry per (b, c >= b)
+  p.u = static_cast<size_t>(o) * 8 * 8;  // U padded to at most 8 LOs
+  auto al = [](size_t x) { return (std::max<size_t>(x, 256) + 255) / 256 * 256; };
+  p.total = 2 * al(p.xt) + 2 * al(p.to) + al(p.ovoo) + al(p.pbvv) + al(p.ovvv_chunk) + al(p.w) + al(p.tpart) +
+            2 * al(p.batch) + al(p.u);
+  return p;
+}
+
 int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   const long long oo = 1LL * o * o, vv = 1LL * v * v, ov = 1LL * o * v, ooo = oo * o;
   const bool bf = mixed;
@@ -558,9 +591,25 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // around each chunk's contraction launches
 
   // ---- operands (packed once per call)
+  const TriplesPlan tp = triples_plan(o, v, N, bf, opts.triples_chunk_mb);
+  if (ws_ext && ws_ext_bytes < tp.total) {
+    set_error("lnocc_triples: attached workspace smaller than lnocc_workspace_bytes (" + std::to_string(tp.total) +
+              " bytes)");
+    return LNOCC_EINVAL;
+  }
   std::vector<void*> mine;
+  size_t ws_used = 0;
+  // temporaries: carved in plan order from the caller's workspace when one is attached (no device
+  // allocation), else allocated in the fragment's memory mode and freed before returning
   auto tmp_alloc = [&](size_t bytes) -> void* {
-    void* p = dev_alloc(std::max<size_t>(bytes, 256));
+    bytes = (std::max<size_t>(bytes, 256) + 255) / 256 * 256;
+    if (ws_ext) {
+      if (ws_used + bytes > ws_ext_bytes) return nullptr;
+      void* p = static_cast<unsigned char*>(ws_ext) + ws_used;
+      ws_used += bytes;
+      return p;
+    }
+    void* p = dev_alloc(bytes);
     if (p) mine.push_back(p);
     return p;
   };
@@ -610,8 +659,8 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       return LNOCC_ENOMEM;
     }
     pack(view(Bvv, kOne, kOne, A_(static_cast<int>(vv), 1), kOne, kOne, A_(N, vv)), PBvv, s);
-    const int bc = static_cast<int>(std::max(1LL, std::min<long long>(v, (1LL << 26) / (o * vv))));
-    double* tmp = static_cast<double*>(tmp_alloc(static_cast<size_t>(bc) * o * vv * 8));
+    const int bc = tp.bc;
+    double* tmp = static_cast<double*>(tmp_alloc(tp.ovvv_chunk));
     if (!tmp) {
       cleanup();
       set_error("lnocc_triples: device allocation failed (ovvv chunk)");
@@ -641,18 +690,10 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 
   // ---- slabs of fixed b: virtual c in [b, v) in chunks, a in [0, b]; W_chunk[c - c0][a][i][j][k]
   const size_t wsz = bf ? 4 : 8;
-  // W chunk: up to 768 MB (fewer, larger contraction launches measured faster than chunks that fit
-  // L2), but never more than the largest slab (b + 1)(v - b) o^3 needs
-  long long chunk_mb = 768;
-  if (const char* e = std::getenv("LNOCC_TCHUNK_MB")) chunk_mb = std::max(1, std::atoi(e));
-  long long max_slab = 0;
-  for (int bb = 0; bb < v; ++bb) max_slab = std::max(max_slab, 1LL * (bb + 1) * (v - bb) * ooo);
-  const long long welems = std::max<long long>(
-      std::min<long long>((chunk_mb << 20) / static_cast<long long>(wsz), max_slab), v * ooo);
-  void* W = tmp_alloc(static_cast<size_t>(welems) * wsz);
-  long long nblk_total = 0;
-  for (int b = 0; b < v; ++b) nblk_total += 1LL * (b + 1) * (v - b);
-  double* tpart = static_cast<double*>(tmp_alloc(static_cast<size_t>(nblk_total) * 2 * 8));
+  const long long welems = tp.welems;
+  void* W = tmp_alloc(tp.w);
+  const long long nblk_total = tp.nblk;
+  double* tpart = static_cast<double*>(tmp_alloc(tp.tpart));
   // chunk plan and the per-c batch tables of the sigma2 / sigma5 terms (uploaded once)
   struct Chunk {
     int b, c0, nc;
@@ -681,8 +722,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       }
     }
   }
-  BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * std::max<size_t>(hbat.size(), 1)));
-  BatchEntry* dbat12 = static_cast<BatchEntry*>(tmp_alloc(sizeof(BatchEntry) * std::max<size_t>(hbat12.size(), 1)));
+  BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(tp.batch));
+  BatchEntry* dbat12 = static_cast<BatchEntry*>(tmp_alloc(tp.batch));
+  if (sizeof(BatchEntry) * hbat.size() > tp.batch || sizeof(BatchEntry) * hbat12.size() > tp.batch) {
+    cleanup();
+    set_error("lnocc_triples: internal error (launch tables larger than planned)");
+    return LNOCC_EINVAL;
+  }
   if (!W || !tpart || !dbat || !dbat12) {
     cleanup();
     set_error("lnocc_triples: device allocation failed (W chunk)");
@@ -703,7 +749,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   const int nlo_t = nlo == 0 ? 0 : nlo <= 1 ? 1 : nlo <= 2 ? 2 : nlo <= 4 ? 4 : 8;
   double* dUp = nullptr;
   if (staged && nlo_t > 0) {
-    dUp = static_cast<double*>(tmp_alloc(static_cast<size_t>(o) * nlo_t * 8));
+    dUp = static_cast<double*>(tmp_alloc(tp.u));
     if (!dUp) {
       cleanup();
       set_error("lnocc_triples: device allocation failed (U)");

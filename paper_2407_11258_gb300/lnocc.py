@@ -28,14 +28,15 @@ EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragme
            "lnocc_version", "lnocc_default_batch_opts", "lnocc_solve_batch", "lnocc_autotune", "lnocc_autotune_save",
            "lnocc_autotune_load", "lnocc_autotune_stats", "lnocc_mlp_nparams", "lnocc_mlp_create", "lnocc_mlp_free",
            "lnocc_mlp_get", "lnocc_mlp_set_norm", "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step",
-           "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp"]
+           "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp", "lnocc_mp2_workspace_bytes",
+           "lnocc_mp2_energy", "lnocc_workspace_bytes", "lnocc_frag_set_workspace", "lnocc_debug_wait"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("diis_space", ctypes.c_int),
                 ("n_refine", ctypes.c_int), ("conv_rms", ctypes.c_double), ("conv_energy", ctypes.c_double),
                 ("fault_inject", ctypes.c_int), ("verbose", ctypes.c_int), ("graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("triples_chunk_mb", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Info(ctypes.Structure):
@@ -45,7 +46,7 @@ class Info(ctypes.Structure):
                 ("model_flops_t", ctypes.c_double), ("exec_flops", ctypes.c_double),
                 ("gemm_launches", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("t_triples_gemm_ms", ctypes.c_double),
-                ("t_triples_ms", ctypes.c_double)]
+                ("t_triples_ms", ctypes.c_double), ("device_allocs", ctypes.c_longlong)]
 
 
 class BatchItem(ctypes.Structure):
@@ -123,6 +124,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("lnocc_mlp_nparams", "lnocc_mlp_create", "lnocc_mlp_free", "lnocc_mlp_get", "lnocc_mlp_set_norm",
                  "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step", "lnocc_mlp_forward",
                  "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp"):
+        getattr(lib, name).restype = I
+    lib.lnocc_debug_wait.argtypes = [I, ctypes.c_longlong, LL, P]
+    lib.lnocc_debug_wait.restype = I
+    lib.lnocc_workspace_bytes.argtypes = [I, I, I, ctypes.POINTER(Opts), LL]
+    lib.lnocc_frag_set_workspace.argtypes = [P, P, ctypes.c_longlong]
+    for name in ("lnocc_workspace_bytes", "lnocc_frag_set_workspace"):
+        getattr(lib, name).restype = I
+    lib.lnocc_mp2_workspace_bytes.argtypes = [I, I, I, I, LL]
+    lib.lnocc_mp2_energy.argtypes = [I, I, I, I, P, P, P, ctypes.c_longlong, ctypes.POINTER(D), P]
+    for name in ("lnocc_mp2_workspace_bytes", "lnocc_mp2_energy"):
         getattr(lib, name).restype = I
     lib.lnocc_last_error.restype = ctypes.c_char_p
     lib.lnocc_version.restype = ctypes.c_char_p
@@ -242,13 +253,14 @@ def lnocc_ccsd(frag: Fragment, t1_in=None, t2_in=None, guess_mode=LNOCC_GUESS_MP
     return e.value, it.value, code
 
 
-def lnocc_fragment_energy(frag: Fragment, U_frag, stream=None):
-    """Returns (e_ccsd_frag, e_mp2_frag); U_frag is [nocc][nlo]."""
+def lnocc_fragment_energy(frag: Fragment, U_frag, stream=None, ccsd=True):
+    """Returns (e_ccsd_frag, e_mp2_frag); U_frag is [nocc][nlo]. ccsd=False asks for the MP2 fragment
+    energy only (no lnocc_ccsd needed; e_ccsd_frag is then None)."""
     _rows(U_frag, _dims(frag)[0])
     ec, em = ctypes.c_double(0.0), ctypes.c_double(0.0)
-    _check(load().lnocc_fragment_energy(frag.h, int(U_frag.shape[1]), _ptr(U_frag), ctypes.byref(ec),
-                                        ctypes.byref(em), _stream(stream)))
-    return ec.value, em.value
+    _check(load().lnocc_fragment_energy(frag.h, int(U_frag.shape[1]), _ptr(U_frag),
+                                        ctypes.byref(ec) if ccsd else None, ctypes.byref(em), _stream(stream)))
+    return (ec.value if ccsd else None), em.value
 
 
 def lnocc_triples(frag: Fragment, U_frag=None, stream=None):
@@ -258,6 +270,28 @@ def lnocc_triples(frag: Fragment, U_frag=None, stream=None):
     nlo = int(U_frag.shape[1]) if U_frag is not None else 0
     _check(load().lnocc_triples(frag.h, nlo, _ptr(U_frag), ctypes.byref(ef), ctypes.byref(eF), _stream(stream)))
     return ef.value, eF.value
+
+
+def lnocc_workspace_bytes(nocc, nvir, naux, opts=None):
+    """Device scratch (bytes) lnocc_triples needs for a fragment of these sizes and options."""
+    b = ctypes.c_longlong(0)
+    _check(load().lnocc_workspace_bytes(nocc, nvir, naux, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    return b.value
+
+
+def lnocc_frag_set_workspace(frag: Fragment, workspace):
+    """Attach a caller-owned CUDA tensor (at least lnocc_workspace_bytes bytes) as the (T) scratch, or
+    detach with None. The fragment keeps a reference so the tensor outlives its use."""
+    if workspace is None:
+        _check(load().lnocc_frag_set_workspace(frag.h, None, 0))
+        frag.workspace = None
+        return
+    import torch
+    if not (isinstance(workspace, torch.Tensor) and workspace.is_cuda and workspace.is_contiguous()):
+        raise TypeError("workspace: expected a contiguous CUDA tensor")
+    _check(load().lnocc_frag_set_workspace(frag.h, workspace.data_ptr(),
+                                           workspace.numel() * workspace.element_size()))
+    frag.workspace = workspace
 
 
 def lnocc_debug_gemm(precision, A, B, C, stream=None):
@@ -270,6 +304,15 @@ def lnocc_debug_gemm(precision, A, B, C, stream=None):
     return C
 
 
+def lnocc_debug_wait(arrive, budget_ns, stream=None):
+    """Bounded-wait diagnostic: returns (status code, nanoseconds the kernel waited); never raises on
+    LNOCC_ETIMEOUT, which is the expected result with arrive=False."""
+    w = ctypes.c_longlong(0)
+    code = load().lnocc_debug_wait(1 if arrive else 0, int(budget_ns), ctypes.byref(w), _stream(stream))
+    _check(code, (LNOCC_OK, LNOCC_ETIMEOUT))
+    return code, w.value
+
+
 def lnocc_gemm_noalloc(precision, A, B, C, stream=None):
     """C = A @ B.T through the contraction engine using the library's fixed scratch (no device allocation)."""
     M, K = A.shape
@@ -278,6 +321,29 @@ def lnocc_gemm_noalloc(precision, A, B, C, stream=None):
     _need(C, M * N, "C")
     _check(load().lnocc_gemm_noalloc(precision, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
     return C
+
+
+def lnocc_mp2_workspace_bytes(precision, nocc, nvir, naux):
+    b = ctypes.c_longlong(0)
+    _check(load().lnocc_mp2_workspace_bytes(precision, nocc, nvir, naux, ctypes.byref(b)))
+    return b.value
+
+
+def lnocc_mp2_energy(precision, nocc, nvir, naux, eps, B_ov, workspace=None, stream=None):
+    """Full-system MP2 correlation energy (Eq. 17's first term) from the ov block B_ov [naux][nocc][nvir].
+    workspace: None (the library allocates) or a CUDA tensor of at least lnocc_mp2_workspace_bytes bytes."""
+    _need(eps, nocc + nvir, "eps")
+    _need(B_ov, naux * nocc * nvir, "B_ov")
+    ws, wsb = None, 0
+    if workspace is not None:
+        import torch
+        if not (isinstance(workspace, torch.Tensor) and workspace.is_cuda and workspace.is_contiguous()):
+            raise TypeError("workspace: expected a contiguous CUDA tensor")
+        ws, wsb = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    e = ctypes.c_double(0.0)
+    _check(load().lnocc_mp2_energy(precision, nocc, nvir, naux, _ptr(eps), _ptr(B_ov), ws, wsb, ctypes.byref(e),
+                                   _stream(stream)))
+    return e.value
 
 
 def default_batch_opts(**kw) -> BatchOpts:
