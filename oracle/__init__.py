@@ -12,7 +12,8 @@ Modules
   triples   LNO-(T) intermediates and the projected (T) energy          -- Eq. 14-16, SI Sec. S1
   fragment  projection of an occupied-pair energy matrix onto LOs       -- Eq. 7-8, Eq. 12, Eq. 15
   mp2       full-system MP2 and the MP2 composite correction            -- Eq. 17, Eq. 12-13, Eq. 21
+  lno       local active space: SVD split, MP2 / CBNO densities, LNOs   -- Sec. II.C-E, Eq. 18-26, Eq. 28
   fci       brute-force two-electron FCI (pin for CCSD)
   spinorb   spin-orbital CCSD and (T) (independent pin for the closed-shell forms)
 """
-from . import ccsd, triples, fragment, fci, spinorb, mp2  # noqa: F401
+from . import ccsd, triples, fragment, fci, spinorb, mp2, lno  # noqa: F401

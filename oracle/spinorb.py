@@ -179,3 +179,65 @@ def to_spin_amplitudes(t1, t2):
             t2s[si::2, sj::2, si::2, sj::2] += t2
             t2s[si::2, sj::2, sj::2, si::2] -= t2.transpose(0, 1, 3, 2)
     return t1s, t2s
+
+
+def restricted_mp2_densities(eps, B, nocc, W_occ=None, f_occ=None, W_vir=None, f_vir=None):
+    """Spin-orbital first-order amplitudes t_IJ^AB = <IJ||AB> / (f_I + f_J - f_A - f_B) in a basis where
+    the occupied (virtual) orbitals are the columns of W_occ (W_vir) followed by the canonical ones, and
+    the MP2 density blocks with occupied / virtual indices restricted to those columns:
+      D_AB(one internal occupied) = sum_{I int} sum_{J C} t_IJ^AC t_IJ^BC,
+      D_IJ(one internal occupied) = sum_{K int} sum_{A B} t_IK^AB t_JK^AB,
+      D_AB(both occupied internal) = sum_{I J int} sum_C t_IJ^AC t_IJ^BC,
+      D_IJ(both virtuals internal) = sum_K sum_{A B int} t_IK^AB t_JK^AB,
+    each summed over spin onto spatial indices (canonical orbitals only; the internal columns act as the
+    restricted index). Returns a dict of those four spatial matrices; an independent route to the
+    closed-shell densities of the local active space (Sec. II.C and II.E)."""
+    e = np.asarray(eps, dtype=np.float64)
+    n = B.shape[1]
+    nvir = n - nocc
+    Bo = np.asarray(B[:, :nocc, nocc:], dtype=np.float64)
+    eo, ev = e[:nocc], e[nocc:]
+    Wo = np.zeros((nocc, 0)) if W_occ is None else np.asarray(W_occ)
+    Wv = np.zeros((nvir, 0)) if W_vir is None else np.asarray(W_vir)
+    fo = np.zeros(0) if f_occ is None else np.asarray(f_occ)
+    fv = np.zeros(0) if f_vir is None else np.asarray(f_vir)
+    no, nv = Wo.shape[1], Wv.shape[1]
+    # extended spatial occupied basis [internal | canonical], virtual [internal | canonical]
+    Co = np.concatenate([Wo, np.eye(nocc)], axis=1)
+    Cv = np.concatenate([Wv, np.eye(nvir)], axis=1)
+    Lov = np.einsum("Qia,iI,aA->QIA", Bo, Co, Cv)
+    eO = np.concatenate([fo, eo])
+    eV = np.concatenate([fv, ev])
+    ovov = np.einsum("QIA,QJB->IAJB", Lov, Lov)       # (IA|JB), spatial
+    mo, mv = eO.size, eV.size
+    # spin orbitals: 2p + s
+    spat_o, spin_o = np.arange(2 * mo) // 2, np.arange(2 * mo) % 2
+    spat_v, spin_v = np.arange(2 * mv) // 2, np.arange(2 * mv) % 2
+    # <IJ|AB> = (IA|JB) d(sI,sA) d(sJ,sB)
+    phys = ovov[np.ix_(spat_o, spat_v, spat_o, spat_v)].transpose(0, 2, 1, 3)
+    same = ((spin_o[:, None, None, None] == spin_v[None, None, :, None])
+            & (spin_o[None, :, None, None] == spin_v[None, None, None, :]))
+    g = phys * same
+    g = g - g.transpose(0, 1, 3, 2)
+    eOs, eVs = eO[spat_o], eV[spat_v]
+    t = g / (eOs[:, None, None, None] + eOs[None, :, None, None] - eVs[None, None, :, None] - eVs[None, None, None, :])
+    io = np.arange(2 * no)                 # internal occupied spin orbitals
+    co = np.arange(2 * no, 2 * mo)         # canonical occupied
+    iv = np.arange(2 * nv)
+    cv = np.arange(2 * nv, 2 * mv)
+
+    def spatial(M, nrow):
+        return M[0::2, 0::2][:nrow, :nrow] + M[1::2, 1::2][:nrow, :nrow]
+
+    out = {}
+    if no:
+        tt = t[np.ix_(io, co, cv, cv)]
+        out["vir_one_int_occ"] = spatial(np.einsum("IJac,IJbc->ab", tt, tt), nvir)
+        tt = t[np.ix_(co, io, cv, cv)]
+        out["occ_one_int_occ"] = spatial(np.einsum("iKab,jKab->ij", tt, tt), nocc)
+        tt = t[np.ix_(io, io, cv, cv)]
+        out["vir_two_int_occ"] = spatial(np.einsum("IJac,IJbc->ab", tt, tt), nvir)
+    if nv:
+        tt = t[np.ix_(co, co, iv, iv)]
+        out["occ_two_int_vir"] = spatial(np.einsum("iKAB,jKAB->ij", tt, tt), nocc)
+    return out
