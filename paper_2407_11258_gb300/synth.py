@@ -187,6 +187,15 @@ def triples_large(seed: int = 4000, scaled: bool = False) -> Fragment:
     return make_fragment(32, 480, 1600, seed, decay=20.0, frag=(0,))
 
 
+def batch_gap(f: int, nfrag: int = 128, seed: int = 3000) -> float:
+    """HOMO-LUMO gap of fragment f of the uneven batch (its energies come from the same stream as
+    batch_fragment / batch_fragment_device), without drawing its B."""
+    o, v, q, small = batch_shapes(nfrag, seed)[f]
+    st_e = Stream(seed + f, 1)
+    eps = small_gap_energies(st_e, o, v) if small else orbital_energies(st_e, o, v, (-1.2, -0.4), (0.3, 4.0))
+    return float(eps[o] - eps[o - 1])
+
+
 def batch_fragment_device(f: int, device, nfrag: int = 128, seed: int = 3000):
     """Fragment f of the uneven batch at full size with B drawn on the device (fragment_device): the CPU
     stream needs minutes for the ~88 GB batch. Orbital energies and U come from the same splitmix64

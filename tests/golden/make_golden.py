@@ -3,6 +3,7 @@
     python tests/golden/make_golden.py small        # nocc=4/nvir=24, (T) at nocc=12/nvir=96, batch subset
     python tests/golden/make_golden.py diamond      # nocc=16, nvir=240, naux=960, CCSD only (about 1.5 h)
     python tests/golden/make_golden.py half         # nocc=16, nvir=120, naux=480 with (T) (about 30 min)
+    python tests/golden/make_golden.py half_li      # same sizes, lithium-like small-gap energies, with (T)
 
 Each file records the generator call that rebuilds the inputs, the oracle's
 energies (FP64) and its convergence data.
@@ -68,6 +69,14 @@ def main(tier):
                "decay=20.0, frag=(0, 1))")
         res = {"half_diamond": dict(gen=gen, **solve(fr, log=log))}
         path = os.path.join(HERE, "oracle_half_diamond.json")
+    elif tier == "half_li":
+        # lithium-like (small-gap) energies at the half-diamond sizes: the regime where the mixed path's
+        # residual noise floor and slow convergence could break the 1e-6 Eh budget (seed 2505: gap 0.040 Eh, the
+        # smallest of the lithium-like range 2 * U[0.02, 0.1])
+        fr = synth.make_fragment(16, 120, 480, 2505, decay=20.0, small_gap=True, frag=(0, 1))
+        gen = "synth.make_fragment(16, 120, 480, 2505, decay=20.0, small_gap=True, frag=(0, 1))"
+        res = {"half_lithium": dict(gen=gen, gap=float(fr.eps[16] - fr.eps[15]), **solve(fr, log=log))}
+        path = os.path.join(HERE, "oracle_half_lithium.json")
     else:
         raise SystemExit(__doc__)
     res["_note"] = "written by tests/golden/make_golden.py from oracle/ only"

@@ -1,8 +1,9 @@
 """Sharding of independent fragments over ranks: world-size-2 gloo processes on the CPU.
 
-Each rank solves its LPT-assigned fragments (here with the CPU oracle standing in for the GPU solver,
-since this pool gives one GPU per box) and the gathered energies, summed in fragment order, must be
-bit-identical to the single-rank sum.
+Each rank takes its share of one fragment list from shard.assign (the LPT split that bench.py's batch
+workload uses on the GPU path), solves it (here with the CPU oracle standing in for the GPU solver,
+since this pool gives one GPU per box), and the energies gathered with shard.gather_energies and summed
+with shard.ordered_sum (the same calls as on the GPU path) must be bit-identical to the single-rank sum.
 """
 import os
 import socket
@@ -28,9 +29,8 @@ def _fragment_energy(f):
 def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    shapes = synth.batch_shapes()[:NFRAG]
-    costs = [shard.fragment_cost(o, v) for o, v, _, _ in shapes]
-    mine = shard.lpt_assign(costs, world)[rank]
+    shapes = [(o, v, q, synth.batch_gap(f)) for f, (o, v, q, _) in enumerate(synth.batch_shapes()[:NFRAG])]
+    mine = shard.assign(shapes, world)[rank]
     local = {f: _fragment_energy(f) for f in mine}
     allE = shard.gather_energies(local, world)
     if rank == 0:
@@ -45,6 +45,17 @@ def _free_port():
     p = s.getsockname()[1]
     s.close()
     return p
+
+
+def test_cost_model_prefers_small_gaps_and_covers_the_list():
+    """The cost grows as the gap closes (more CCSD iterations) and every fragment is assigned once."""
+    assert shard.fragment_cost(16, 240, 960, 0.05) > shard.fragment_cost(16, 240, 960, 0.7)
+    shapes = [(o, v, q, synth.batch_gap(f)) for f, (o, v, q, _) in enumerate(synth.batch_shapes())]
+    parts = shard.assign(shapes, 4)
+    assert sorted(sum(parts, [])) == list(range(128))
+    costs = [shard.fragment_cost(*s) for s in shapes]
+    loads = [sum(costs[i] for i in p) for p in parts]
+    assert max(loads) - min(loads) <= max(costs)  # LPT bound
 
 
 def test_lpt_assignment_balances_and_covers():
