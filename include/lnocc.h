@@ -231,6 +231,72 @@ int lnocc_mp2_energy(int precision, int nocc, int nvir, int naux, const double* 
                      void* workspace, long long workspace_bytes, double* e_mp2, void* stream);
 
 /* ------------------------------------------------------------------------------------------------
+ * Local active space of a fragment (Sec. II.C; CBNOs of Sec. II.E). For a fragment F with LO coefficients
+ * U^(F) in the canonical occupied (and, for LOs that overlap the virtual space, virtual) orbitals of the
+ * system: the internal orbitals (Eq. 18-19), the MP2 densities that rank the external orbitals (Eq. 20 or
+ * Eq. 28, from the MP1 amplitudes of Eq. 21 with the DF integrals of Eq. 22 at the Gamma point), the LNOs
+ * kept by the thresholds of Eq. 24-26, and the semi-canonical active space with its DF factors, which is
+ * the input of lnocc_build_ints. Real orbitals; all arrays are device FP64, row-major. Each call allocates
+ * its own temporaries and synchronizes `stream`.
+ * ---------------------------------------------------------------------------------------------- */
+#define LNOCC_LNO_MP2 0  /* Eq. 20: one occupied index of the MP2 density restricted to the internal space */
+#define LNOCC_LNO_CBNO 1 /* Eq. 28: both virtual (occupied block) / both occupied (virtual block) internal */
+
+/*
+ * lnocc_lno_internal -- Eq. 18-19 for one block (occupied or virtual): the left singular vectors of
+ * U [n][nlo] with singular value above sv_tol times the largest (0 < sv_tol < 1; 1e-10 is a good choice)
+ * span the internal space; they are returned semi-canonical: the block Fock matrix (diagonal e [n] in
+ * the canonical basis) is diagonalised inside the internal space, f_int [nlo] receives its eigenvalues
+ * in increasing order (first *n_int used) and W_int [n][nlo] the orbitals as columns (first *n_int used,
+ * the rest zero). 1 <= nlo <= 256. *n_int (host) is the internal dimension.
+ */
+int lnocc_lno_internal(int n, int nlo, const double* U, const double* e, double sv_tol, double* W_int, double* f_int,
+                       int* n_int, void* stream);
+
+/*
+ * lnocc_lno_densities -- the occupied block D_occ [nocc][nocc] and virtual block D_vir [nvir][nvir] of the
+ * MP2 density used to rank the external orbitals of fragment F:
+ *   kind LNOCC_LNO_MP2 (Eq. 20):  D_ij = 2 sum_kF sum_ab t_{iakFb} (2 t_{jakFb} - t_{jbkFa}),
+ *     D_ab = sum_iF sum_jc 2 (t_{iFajc} t_{iFbjc} + t_{iFcja} t_{iFcjb}) - (t_{iFcja} t_{iFbjc} + t_{iFajc} t_{iFcjb});
+ *   kind LNOCC_LNO_CBNO (Eq. 28): D_ij = 2 sum_{aF bF} sum_k t_{iaFkbF} (2 t_{jaFkbF} - t_{jbFkaF}),
+ *     D_ab = 2 sum_{iF jF} sum_c t_{iFajFc} (2 t_{iFbjFc} - t_{iFcjFb}) (n_iv = 0 gives D_occ = 0);
+ * with t_{pa qb} = (pa|qb) / (f_p + f_q - f_a - f_b), (ia|jb) = sum_Q B_Qia B_Qjb, canonical energies eps
+ * [nocc + nvir] for canonical orbitals and f_occ / f_vir for the internal ones W_occ [nocc][n_io] /
+ * W_vir [nvir][n_iv] (semi-canonical, as lnocc_lno_internal returns them, leading dimension n_io / n_iv).
+ *   B_ov [naux][nocc][nvir] : the system's occupied-virtual DF block.
+ *   precision : LNOCC_PREC_MIXED contracts as BF16x3 products with FP32 accumulation, LNOCC_PREC_FP64 in FP64;
+ *               amplitudes, denominators and the outputs are FP64. Both blocks are returned symmetric.
+ */
+int lnocc_lno_densities(int precision, int kind, int nocc, int nvir, int naux, const double* eps, const double* B_ov,
+                        int n_io, const double* W_occ, const double* f_occ, int n_iv, const double* W_vir,
+                        const double* f_vir, double* D_occ, double* D_vir, void* stream);
+
+/*
+ * lnocc_lno_select -- Eq. 24-26: the density D [n][n] restricted to the external space (the complement of
+ * the n_int columns of W_int [n][n_int], orthonormal; n_int = 0 keeps the whole space) is diagonalised and the
+ * eigenpairs with |lambda| >= eta are kept, in decreasing order of lambda: C [n][n] receives the LNOs as its
+ * first *n_keep columns (the rest zero) and lambda [n] their eigenvalues (the rest zero). The projection is
+ * P D P with P = 1 - W_int W_int^T, whose eigenvectors of non-zero eigenvalue are the W_bar X of Eq. 25.
+ * 1 <= n <= 8192; FP64 Jacobi eigendecomposition on the device.
+ */
+int lnocc_lno_select(int n, const double* D, int n_int, const double* W_int, double eta, double* C, double* lambda,
+                     int* n_keep, void* stream);
+
+/*
+ * lnocc_active_space -- the fragment's active space in semi-canonical form and its DF factors: the occupied
+ * orbitals C_occ [nocc][no_F] and virtual orbitals C_vir [nvir][nv_F] (orthonormal columns, e.g. internal and
+ * kept LNOs) are rotated so that the Fock matrix (diagonal eps [nocc + nvir] in the canonical basis) is
+ * diagonal inside each block; eps_F [no_F + nv_F] receives the orbital energies (occupied, then virtual,
+ * each increasing) and B_F [naux][nF][nF] (nF = no_F + nv_F) the DF factors C_F^T B[Q] C_F of the system's
+ * B [naux][n][n] (the Gamma-point real form of Eq. 27). C_F [n][nF] (may be NULL) receives the rotated
+ * orbitals (block diagonal: occupied rows and columns first); a fragment's LO matrix in the active occupied
+ * basis is then C_F[:nocc, :no_F]^T U^(F). precision as for lnocc_lno_densities.
+ */
+int lnocc_active_space(int precision, int nocc, int nvir, int naux, const double* eps, const double* B, int no_F,
+                       const double* C_occ, int nv_F, const double* C_vir, double* eps_F, double* B_F, double* C_F,
+                       void* stream);
+
+/* ------------------------------------------------------------------------------------------------
  * Batched fragments.
  *
  * The total correlation energy is a sum of fragment contributions (Eq. ecorr_cc, Sec. 2.2) and each

@@ -109,3 +109,19 @@ def external_spectrum(D, W_ext):
     """All eigenvalues of the external-space density W_ext^T D W_ext, decreasing."""
     Dbar = W_ext.T @ D @ W_ext
     return np.sort(np.linalg.eigvalsh(0.5 * (Dbar + Dbar.T)))[::-1]
+
+
+def active_space(eps, B, nocc, C_occ, C_vir):
+    """The fragment's active space in semi-canonical form (the input of the fragment CCSD, Sec. II.B):
+    the Fock matrix (diagonal eps in the canonical basis) is diagonalised inside span(C_occ) and inside
+    span(C_vir); returns (eps_F increasing within each block, B_F[Q] = C_F^T B[Q] C_F, C_F [n][nF] block
+    diagonal) with the Gamma-point real DF factors B [naux][n][n] of Eq. 27."""
+    e = np.asarray(eps, dtype=np.float64)
+    fo, Ro = np.linalg.eigh(C_occ.T @ np.diag(e[:nocc]) @ C_occ)
+    fv, Rv = np.linalg.eigh(C_vir.T @ np.diag(e[nocc:]) @ C_vir)
+    n = e.size
+    no, nv = C_occ.shape[1], C_vir.shape[1]
+    CF = np.zeros((n, no + nv))
+    CF[:nocc, :no] = C_occ @ Ro
+    CF[nocc:, no:] = C_vir @ Rv
+    return np.concatenate([fo, fv]), np.einsum("ps,Qpq,qt->Qst", CF, B, CF, optimize=True), CF

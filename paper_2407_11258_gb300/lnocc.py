@@ -21,6 +21,7 @@ ERR_NAMES = {0: "LNOCC_OK", 1: "LNOCC_EINVAL", 2: "LNOCC_ENOMEM", 3: "LNOCC_ENOC
              5: "LNOCC_ETIMEOUT", 6: "LNOCC_ECUDA"}
 
 LNOCC_ORDER_LPT, LNOCC_ORDER_INPUT = 0, 1
+LNOCC_LNO_MP2, LNOCC_LNO_CBNO = 0, 1
 NFEAT = 8  # features per amplitude of the learned guess: X is [n][8]
 
 EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragment_energy", "lnocc_triples",
@@ -29,7 +30,8 @@ EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragme
            "lnocc_autotune_load", "lnocc_autotune_stats", "lnocc_mlp_nparams", "lnocc_mlp_create", "lnocc_mlp_free",
            "lnocc_mlp_get", "lnocc_mlp_set_norm", "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step",
            "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp", "lnocc_mp2_workspace_bytes",
-           "lnocc_mp2_energy", "lnocc_workspace_bytes", "lnocc_frag_set_workspace", "lnocc_debug_wait"]
+           "lnocc_mp2_energy", "lnocc_workspace_bytes", "lnocc_frag_set_workspace", "lnocc_debug_wait",
+           "lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space"]
 
 
 class Opts(ctypes.Structure):
@@ -124,6 +126,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("lnocc_mlp_nparams", "lnocc_mlp_create", "lnocc_mlp_free", "lnocc_mlp_get", "lnocc_mlp_set_norm",
                  "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step", "lnocc_mlp_forward",
                  "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp"):
+        getattr(lib, name).restype = I
+    lib.lnocc_lno_internal.argtypes = [I, I, P, P, D, P, P, ctypes.POINTER(I), P]
+    lib.lnocc_lno_densities.argtypes = [I, I, I, I, I, P, P, I, P, P, I, P, P, P, P, P]
+    lib.lnocc_lno_select.argtypes = [I, P, I, P, D, P, P, ctypes.POINTER(I), P]
+    lib.lnocc_active_space.argtypes = [I, I, I, I, P, P, I, P, I, P, P, P, P, P]
+    for name in ("lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space"):
         getattr(lib, name).restype = I
     lib.lnocc_debug_wait.argtypes = [I, ctypes.c_longlong, LL, P]
     lib.lnocc_debug_wait.restype = I
@@ -344,6 +352,78 @@ def lnocc_mp2_energy(precision, nocc, nvir, naux, eps, B_ov, workspace=None, str
     _check(load().lnocc_mp2_energy(precision, nocc, nvir, naux, _ptr(eps), _ptr(B_ov), ws, wsb, ctypes.byref(e),
                                    _stream(stream)))
     return e.value
+
+
+# ------------------------------------------------------------------------------ local active space
+def _empty(*shape, like):
+    import torch
+    return torch.zeros(*shape, dtype=torch.float64, device=like.device)
+
+
+def lnocc_lno_internal(U, e, sv_tol=1e-10, stream=None):
+    """Internal orbitals of one block (Eq. 18-19), semi-canonical. U [n][nlo], e [n]. Returns
+    (W_int [n][n_int], f_int [n_int], n_int) as new CUDA tensors (contiguous)."""
+    n, nlo = U.shape
+    _need(e, n, "e")
+    W = _empty(n, nlo, like=U)
+    f = _empty(nlo, like=U)
+    ni = ctypes.c_int(0)
+    _check(load().lnocc_lno_internal(n, nlo, _ptr(U), _ptr(e), sv_tol, _ptr(W), _ptr(f), ctypes.byref(ni),
+                                     _stream(stream)))
+    k = ni.value
+    return W[:, :k].contiguous(), f[:k].contiguous(), k
+
+
+def lnocc_lno_densities(precision, kind, nocc, nvir, naux, eps, B_ov, W_occ, f_occ, W_vir=None, f_vir=None,
+                        stream=None):
+    """D_occ [nocc][nocc], D_vir [nvir][nvir] (Eq. 20 for kind LNOCC_LNO_MP2, Eq. 28 for LNOCC_LNO_CBNO)."""
+    _need(eps, nocc + nvir, "eps")
+    _need(B_ov, naux * nocc * nvir, "B_ov")
+    n_io = int(W_occ.shape[1])
+    _need(W_occ, nocc * n_io, "W_occ")
+    _need(f_occ, n_io, "f_occ")
+    n_iv = int(W_vir.shape[1]) if W_vir is not None else 0
+    if W_vir is not None:
+        _need(W_vir, nvir * n_iv, "W_vir")
+        _need(f_vir, n_iv, "f_vir")
+    Do = _empty(nocc, nocc, like=B_ov)
+    Dv = _empty(nvir, nvir, like=B_ov)
+    _check(load().lnocc_lno_densities(precision, kind, nocc, nvir, naux, _ptr(eps), _ptr(B_ov), n_io, _ptr(W_occ),
+                                      _ptr(f_occ), n_iv, _ptr(W_vir), _ptr(f_vir), _ptr(Do), _ptr(Dv),
+                                      _stream(stream)))
+    return Do, Dv
+
+
+def lnocc_lno_select(D, W_int=None, eta=0.0, stream=None):
+    """LNOs of Eq. 24-26: returns (C [n][n_keep], lambda [n_keep], n_keep)."""
+    n = int(D.shape[0])
+    _need(D, n * n, "D")
+    n_int = int(W_int.shape[1]) if W_int is not None else 0
+    if W_int is not None:
+        _need(W_int, n * n_int, "W_int")
+    C = _empty(n, n, like=D)
+    lam = _empty(n, like=D)
+    k = ctypes.c_int(0)
+    _check(load().lnocc_lno_select(n, _ptr(D), n_int, _ptr(W_int), float(eta), _ptr(C), _ptr(lam), ctypes.byref(k),
+                                   _stream(stream)))
+    return C[:, :k.value].contiguous(), lam[:k.value].contiguous(), k.value
+
+
+def lnocc_active_space(precision, nocc, nvir, naux, eps, B, C_occ, C_vir, stream=None):
+    """Semi-canonical active space: returns (eps_F [nF], B_F [naux][nF][nF], C_F [n][nF])."""
+    n = nocc + nvir
+    no, nv = int(C_occ.shape[1]), int(C_vir.shape[1])
+    _need(eps, n, "eps")
+    _need(B, naux * n * n, "B")
+    _need(C_occ, nocc * no, "C_occ")
+    _need(C_vir, nvir * nv, "C_vir")
+    nF = no + nv
+    eF = _empty(nF, like=B)
+    BF = _empty(naux, nF, nF, like=B)
+    CF = _empty(n, nF, like=B)
+    _check(load().lnocc_active_space(precision, nocc, nvir, naux, _ptr(eps), _ptr(B), no, _ptr(C_occ), nv,
+                                     _ptr(C_vir), _ptr(eF), _ptr(BF), _ptr(CF), _stream(stream)))
+    return eF, BF, CF
 
 
 def default_batch_opts(**kw) -> BatchOpts:

@@ -74,7 +74,7 @@ def test_attached_workspace_means_no_allocation_after_build(lnocc, shape, prec):
 
 
 def test_workspace_size_follows_the_chunk_option_and_is_checked(lnocc):
-    o, v, q = 6, 40, 160
+    o, v, q = 8, 60, 240  # largest (T) slab ~1.9 MB of FP32 W: a 1 MB chunk bound takes effect
     fr = synth.make_fragment(o, v, q, 950, decay=20.0, frag=(0,))
     big = lnocc.lnocc_workspace_bytes(o, v, q, lnocc.default_opts(precision=1))
     small = lnocc.lnocc_workspace_bytes(o, v, q, lnocc.default_opts(precision=1, triples_chunk_mb=1))
