@@ -509,6 +509,8 @@ def main():
     ap.add_argument("--iters", type=int, default=4, help="case workload: CCSD iteration cap")
     ap.add_argument("--fp64", action="store_true", help="case workload: plain FP64 path")
     ap.add_argument("--mlp-guess", action="store_true", help="case workload: also run the learned-guess kernel once")
+    ap.add_argument("--tchunk", type=int, default=0, help="case workload: (T) W chunk bound in MB (0: library default)")
+    ap.add_argument("--repeat", type=int, default=1, help="case workload: lnocc_triples calls (the last one is printed)")
     ap.add_argument("--ntrain", type=int, default=2000, help="mlp workload: training solves")
     ap.add_argument("--nheld", type=int, default=256, help="mlp workload: held-out fragments")
     ap.add_argument("--train-steps", type=int, default=2000)
@@ -685,7 +687,8 @@ def run_case(args):
     fr = synth.make_fragment(o, v, q, 2024, decay=20.0, frag=(0, 1) if o > 1 else (0,))
     eps, B, U = (torch.tensor(x, device="cuda") for x in (fr.eps, fr.B, fr.U_frag))
     prec = lnocc.LNOCC_PREC_FP64 if args.fp64 else lnocc.LNOCC_PREC_MIXED
-    f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=prec, max_iter=args.iters))
+    f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=prec, max_iter=args.iters,
+                                                                     triples_chunk_mb=args.tchunk))
     t0 = time.perf_counter()
     e, it, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
     t1 = time.perf_counter()
@@ -700,9 +703,11 @@ def run_case(args):
         torch.cuda.synchronize()
         out += f"; learned guess {1e3 * (time.perf_counter() - tg):.2f} ms"
         m.free()
-    et, etf = lnocc.lnocc_triples(f, U)
+    for _ in range(max(1, args.repeat)):
+        et, etf = lnocc.lnocc_triples(f, U)
     inf = f.info()
-    out += (f"; (T) device {inf.t_triples_ms:.1f} ms (contractions {inf.t_triples_gemm_ms:.1f} ms)"
+    out += (f"; (T) chunk {args.tchunk or 768} MB: device {inf.t_triples_ms:.1f} ms (contractions "
+            f"{inf.t_triples_gemm_ms:.1f} ms)"
             f" E_T={et:.12f} E_T_frag={etf:.12f}")
     f.free()
     print(out, flush=True)
