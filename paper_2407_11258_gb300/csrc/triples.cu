@@ -493,208 +493,6 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
   }
 }
 
-// Block energy of the mixed path, slot-contracted form (same block, same inputs and outputs as
-// k_t_energy_f32, far fewer instructions). With placements q of (i, j, k) into the slots of W^{abc}_y
-// (PM below) and, for ordering pi = (p0, p1, p2), the four placements A = (p0, p1, p2), B = (p1, p2, p0),
-// C = (p2, p0, p1), D = (p2, p1, p0) (z = 4 w_A + w_B + w_C, y = v_A - v_D):
-//  * canonical part: sum_ijk w_q(ijk) v_r(ijk) = sum_y w_y v_{y o kappa} with the slot permutation kappa
-//    taking placement q to r, so the block sum is sum_y w_y sum_kappa C_kappa v_{y o kappa}; the six
-//    coefficients C_kappa collect +4 (A,A), -4 (A,D), +1 (B,A), -1 (B,D), +1 (C,A), -1 (C,D) over the
-//    active orderings;
-//  * projected part: sum_i U_i,alpha w_q(ijk) contracts slot PM[q][0] of the block with U[:, alpha], so
-//    with Cw[s][alpha][u][t] = sum_{y_s} U[y_s][alpha] w_y (u, t the remaining slots in increasing order;
-//    Cv likewise) the sum over (j, k) of (sum_i U z)(sum_i' U y) is assembled from table lookups.
-// The i-sums and products run in FP32 as in k_t_energy_f32; block sums in FP64.
-template <int NLO>
-__global__ void __launch_bounds__(256) k_t_energy_slots(const float* __restrict__ W, long long slot_stride, int b,
-                                                        int c0, int o, int v, const double* __restrict__ eps,
-                                                        const double* __restrict__ t1, const double* __restrict__ ovov,
-                                                        const double* __restrict__ U, double* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int NL = NLO > 0 ? NLO : 1;
-  const int slot = blockIdx.y, a = blockIdx.x;
-  const int c = c0 + slot;
-  const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
-  const int o2 = o * o, o3 = o2 * o;
-  const int S1 = o + 1, S0 = o * S1 + 1;
-  const int blk = o * S0;
-  float2* swv = reinterpret_cast<float2*>(smraw);              // (w, v) at y0 * S0 + y1 * S1 + y2
-  float2* cwv = swv + blk;                                        // [3][NL][o2] (Cw, Cv)
-  float* fs = reinterpret_cast<float*>(cwv + 3 * NL * o2);
-  const int P1 = o + 1, o2p = o * P1;
-  float* Sab = fs;
-  float* Sac = Sab + o2p;
-  float* Sbc = Sac + o2p;
-  float* ta = Sbc + o2p;
-  float* tb = ta + o;
-  float* tc = tb + o;
-  float* dm = tc + o;
-  float* Us = dm + o;  // U[i][alpha]
-  __shared__ float Ck[6];
-  const long long ov = 1LL * o * v;
-  const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
-  for (int idx = threadIdx.x; idx < o2; idx += blockDim.x) {
-    const int p = idx / o, q = idx % o;
-    Sab[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + b]);
-    Sac[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + c]);
-    Sbc[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + b) * ov + 1LL * q * v + c]);
-  }
-  for (int y = threadIdx.x; y < o; y += blockDim.x) {
-    ta[y] = static_cast<float>(t1[y * v + a]);
-    tb[y] = static_cast<float>(t1[y * v + b]);
-    tc[y] = static_cast<float>(t1[y * v + c]);
-    dm[y] = static_cast<float>(ex3 - eps[y]);
-  }
-  for (int idx = threadIdx.x; idx < o * NLO; idx += blockDim.x) Us[idx] = static_cast<float>(U[idx]);
-  // placements and the distinct orderings of the labels (a, b, c)
-  constexpr int PM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  const int x0 = a, x1 = b, x2 = c;
-  auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
-  auto idx2 = [](int s0, int s1) { return s0 == 0 ? (s1 == 1 ? 0 : 1) : (s0 == 1 ? (s1 == 0 ? 2 : 3) : (s1 == 0 ? 4 : 5)); };
-  bool act[6];
-#pragma unroll
-  for (int pi = 0; pi < 6; ++pi) {
-    bool dup = false;
-#pragma unroll
-    for (int q = 0; q < pi; ++q)
-      dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
-    act[pi] = !dup;
-  }
-  if (threadIdx.x == 0) {
-    // kappa taking placement qs to qt: kappa(PM[qt][m]) = PM[qs][m]; indexed by idx2(kappa(0), kappa(1))
-    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int pi = 0; pi < 6; ++pi) {
-      if (!act[pi]) continue;
-      const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
-      const int qA = idx2(p0, p1), qB = idx2(p1, p2), qC = idx2(p2, p0), qD = idx2(p2, p1);
-      const int qs[6] = {qA, qA, qB, qB, qC, qC};
-      const int qt[6] = {qA, qD, qA, qD, qA, qD};
-      const float cf[6] = {4.f, -4.f, 1.f, -1.f, 1.f, -1.f};
-      for (int t = 0; t < 6; ++t) {
-        int kap[3];
-        for (int m = 0; m < 3; ++m) kap[PM[qt[t]][m]] = PM[qs[t]][m];
-        C[idx2(kap[0], kap[1])] += cf[t];
-      }
-    }
-    for (int q = 0; q < 6; ++q) Ck[q] = C[q];
-  }
-  __syncthreads();
-  // stage w = W s and v = (W + disconnected) s (W stored [y0][y2][y1], read in that order)
-  const float* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
-  {
-    constexpr int kLoads = 8;
-    const int st = blockDim.x, d1 = st % o, d2 = (st / o) % o, d0 = st / o2;
-    int y1 = threadIdx.x % o, y2 = (threadIdx.x / o) % o, y0 = threadIdx.x / o2;
-    for (int base = threadIdx.x; base < o3; base += kLoads * st) {
-      float wr[kLoads];
-#pragma unroll
-      for (int u = 0; u < kLoads; ++u) wr[u] = base + u * st < o3 ? Wb[base + u * st] : 0.f;
-#pragma unroll
-      for (int u = 0; u < kLoads; ++u) {
-        if (base + u * st < o3) {
-          const float disc = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
-          const float sc = rsqrtf(dm[y0] + dm[y1] + dm[y2]);
-          swv[y0 * S0 + y1 * S1 + y2] = make_float2(wr[u] * sc, (wr[u] + disc) * sc);
-        }
-        y1 += d1;
-        int cy = y1 >= o;
-        y1 -= cy ? o : 0;
-        y2 += d2 + cy;
-        cy = y2 >= o;
-        y2 -= cy ? o : 0;
-        y0 += d0 + cy;
-      }
-    }
-  }
-  __syncthreads();
-  float r_can = 0.f, r_frag = 0.f;
-  // canonical part: sum_y w_y sum_kappa C_kappa v_{y o kappa}
-  {
-    float Cl[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) Cl[q] = Ck[q];
-    for (int y = threadIdx.x; y < o3; y += blockDim.x) {
-      const int yy[3] = {y / o2, (y / o) % o, y % o};
-      const float2 wv0 = swv[yy[0] * S0 + yy[1] * S1 + yy[2]];
-      float Y = 0.f;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        if (Cl[q] != 0.f) {
-          const int k0 = PM[q][0], k1 = PM[q][1], k2 = PM[q][2];  // kappa = (k0, k1, k2): slot s reads y[kappa(s)]
-          Y += Cl[q] * swv[yy[k0] * S0 + yy[k1] * S1 + yy[k2]].y;
-        }
-      }
-      r_can += wv0.x * Y;
-    }
-  }
-  if (NLO > 0) {
-    // slot contractions: cwv[s][al][u * o + t] = sum_{y_s} U[y_s][al] (w, v)_y
-    for (int item = threadIdx.x; item < 3 * o2; item += blockDim.x) {
-      const int sl = item / o2, u = (item % o2) / o, t = item % o;
-      // the remaining slots r0 < r1 carry u, t
-      const int r0 = sl == 0 ? 1 : 0, r1 = sl == 2 ? 1 : 2;
-      const int stride_s = sl == 0 ? S0 : (sl == 1 ? S1 : 1);
-      const int base = u * (r0 == 0 ? S0 : S1) + t * (r1 == 1 ? S1 : 1);
-      float2 acc[NL];
-#pragma unroll
-      for (int al = 0; al < NL; ++al) acc[al] = make_float2(0.f, 0.f);
-      for (int ys = 0; ys < o; ++ys) {
-        const float2 wv = swv[base + ys * stride_s];
-#pragma unroll
-        for (int al = 0; al < NLO; ++al) {
-          const float uu = Us[ys * NLO + al];
-          acc[al].x = fmaf(uu, wv.x, acc[al].x);
-          acc[al].y = fmaf(uu, wv.y, acc[al].y);
-        }
-      }
-#pragma unroll
-      for (int al = 0; al < NLO; ++al) cwv[(sl * NL + al) * o2 + u * o + t] = acc[al];
-    }
-    __syncthreads();
-    // projected part: per active ordering, LO and (j, k): (4 Cw_A + Cw_B + Cw_C)(Cv_A - Cv_D)
-    auto look = [&](int q, int al, int j, int k) {
-      const int s = PM[q][0], sj = PM[q][1], sk = PM[q][2];
-      const int u = sj < sk ? j : k, t = sj < sk ? k : j;
-      return cwv[(s * NL + al) * o2 + u * o + t];
-    };
-    for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
-      const int j = jk / o, k = jk % o;
-#pragma unroll
-      for (int pi = 0; pi < 6; ++pi) {
-        if (!act[pi]) continue;
-        const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
-        const int qA = idx2(p0, p1), qB = idx2(p1, p2), qC = idx2(p2, p0), qD = idx2(p2, p1);
-#pragma unroll
-        for (int al = 0; al < NLO; ++al) {
-          const float2 A = look(qA, al, j, k), Bq = look(qB, al, j, k), Cq = look(qC, al, j, k), D = look(qD, al, j, k);
-          r_frag += (4.f * A.x + Bq.x + Cq.x) * (A.y - D.y);
-        }
-      }
-    }
-  }
-  double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
-  __shared__ double sh[2][32];
-  for (int off = 16; off > 0; off >>= 1) {
-    e_can += __shfl_xor_sync(0xffffffffu, e_can, off);
-    e_frag += __shfl_xor_sync(0xffffffffu, e_frag, off);
-  }
-  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  if (l == 0) {
-    sh[0][w] = e_can;
-    sh[1][w] = e_frag;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
-      s0 += sh[0][q];
-      s1 += sh[1][q];
-    }
-    out[2 * blk_id] = -s0 / 3.0;
-    out[2 * blk_id + 1] = -s1 / 3.0;
-  }
-}
-
 // Sum of the per-block partials in a fixed order: out[0] canonical, out[1] projected.
 __global__ void k_t_finish(const double* part, long long nblk, double* out) {
   __shared__ double sh[2][32];
@@ -960,21 +758,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     cudaMemsetAsync(dUp, 0, static_cast<size_t>(o) * nlo_t * 8, s);
     cudaMemcpy2DAsync(dUp, nlo_t * 8, U, nlo * 8, nlo * 8, o, cudaMemcpyDeviceToDevice, s);
   }
-  // slot-contracted FP32 kernel: the staged (w, v) block plus 3 * max(nlo_t, 1) o^2 (Cw, Cv) pairs
-  const long long slots_smem = 8LL * sblk + 8LL * 3 * std::max(nlo_t, 1) * oo +
-                               4LL * (3LL * o * (o + 1) + 4LL * o + 1LL * o * std::max(nlo_t, 1)) + 16;
-  const bool use_slots = bf && staged_full && slots_smem <= 200LL * 1024;
   auto energy_launch = [&](const void* Wp, long long Sc, int b, int c0, int na, int nc, double* part) {
     dim3 grid(na, nc);
     count_launch();
-    // FP32 W with w and v staged: the slot-contracted kernel when its tables fit, else k_t_energy_f32;
-    // otherwise the generic staged kernel
+    // FP32 W with w and v staged: k_t_energy_f32; otherwise the generic staged kernel
 #define LN_F(K)                                                                                          \
   do {                                                                                                   \
-    if (use_slots)                                                                                       \
-      k_t_energy_slots<K><<<grid, 256, slots_smem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps, \
-                                                        t1, ovov, dUp, part);                            \
-    else if (staged_full)                                                                                \
+    if (staged_full)                                                                                     \
       k_t_energy_f32<K><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps, t1,  \
                                                  ovov, dUp, part);                                       \
     else                                                                                                 \
@@ -1027,11 +817,6 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       attr(reinterpret_cast<const void*>(k_t_energy_f32<2>));
       attr(reinterpret_cast<const void*>(k_t_energy_f32<4>));
       attr(reinterpret_cast<const void*>(k_t_energy_f32<8>));
-      attr(reinterpret_cast<const void*>(k_t_energy_slots<0>));
-      attr(reinterpret_cast<const void*>(k_t_energy_slots<1>));
-      attr(reinterpret_cast<const void*>(k_t_energy_slots<2>));
-      attr(reinterpret_cast<const void*>(k_t_energy_slots<4>));
-      attr(reinterpret_cast<const void*>(k_t_energy_slots<8>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, false>));
