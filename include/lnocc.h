@@ -296,6 +296,22 @@ int lnocc_active_space(int precision, int nocc, int nvir, int naux, const double
                        const double* C_occ, int nv_F, const double* C_vir, double* eps_F, double* B_F, double* C_F,
                        void* stream);
 
+/*
+ * lnocc_kpoint_df -- integrals of the local Hamiltonian from k-point DF factors (Eq. 27a),
+ * V_pqrs = sum_q sum_P L^P_pq(q) L^P_rs(-q), reduced to the real form (pq|rs) = sum_Q B_Qpq B_Qrs that
+ * lnocc_build_ints takes.
+ *   L [nk][naux][n][n] : complex factors (device, interleaved real/imaginary FP64) of the nk momentum
+ *                        transfers q in the basis of the n active orbitals (real orbitals: L_pq(q) = L_qp(q),
+ *                        L(-q) = conj L(q); checked, LNOCC_EINVAL beyond 1e-10 of max |L|).
+ *   qneg [nk] (host)   : index of -q for each q (an involution).
+ *   B_out [nk * naux][n][n] (device) : sqrt(2) Re L(q) and sqrt(2) Im L(q) for one q of each pair (q, -q),
+ *                        Re L(q) for each self-conjugate q, in increasing q: sum_Q B_Qpq B_Qrs equals V_pqrs.
+ *   sym_err (host, may be NULL) : the largest symmetry deviation relative to max |L|.
+ * Allocates a small table and synchronizes `stream`.
+ */
+int lnocc_kpoint_df(int nk, int naux, int n, const double* L, const int* qneg, double* B_out, double* sym_err,
+                    void* stream);
+
 /* ------------------------------------------------------------------------------------------------
  * Batched fragments.
  *

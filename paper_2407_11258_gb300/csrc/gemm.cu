@@ -695,11 +695,8 @@ __global__ void __launch_bounds__(256, 1)
         const bool rowv4 = mvalid && (reinterpret_cast<uintptr_t>(rowp) & 15) == 0;
         const float al = p.alpha_f;
         const bool acc_mode = p.beta_f == 1.f;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          float v[16];
-          tmem_ld16(acc + c0, v);
-          if (!mvalid) continue;
+        // 16 accumulator columns starting at c0 (values v) to the destination row
+        auto emit16 = [&](const float* v, int c0) {
 #pragma unroll
           for (int g4 = 0; g4 < 4; ++g4) {
             const int q = (c0 >> 2) + g4;
@@ -721,6 +718,22 @@ __global__ void __launch_bounds__(256, 1)
                   rowp[co] = al * v[4 * g4 + k];
               }
             }
+          }
+        };
+        // 32 columns per TMEM load (one wait per 32 columns instead of per 16); a 16-column tail for BN = 144
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          if (c0 + 32 <= BN) {
+            float v[32];
+            tmem_ld32(acc + c0, v);
+            if (!mvalid) continue;
+            emit16(v, c0);
+            emit16(v + 16, c0 + 16);
+          } else {
+            float v[16];
+            tmem_ld16(acc + c0, v);
+            if (!mvalid) continue;
+            emit16(v, c0);
           }
         }
       } else if (p.ws) {  // split-K partials, FP64 row-major [z][M][N]

@@ -31,7 +31,8 @@ EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragme
            "lnocc_mlp_get", "lnocc_mlp_set_norm", "lnocc_mlp_samples", "lnocc_mlp_fit_norm", "lnocc_mlp_train_step",
            "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp", "lnocc_mp2_workspace_bytes",
            "lnocc_mp2_energy", "lnocc_workspace_bytes", "lnocc_frag_set_workspace", "lnocc_debug_wait",
-           "lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space"]
+           "lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space",
+           "lnocc_kpoint_df"]
 
 
 class Opts(ctypes.Structure):
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lnocc_active_space.argtypes = [I, I, I, I, P, P, I, P, I, P, P, P, P, P]
     for name in ("lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space"):
         getattr(lib, name).restype = I
+    lib.lnocc_kpoint_df.argtypes = [I, I, I, P, ctypes.POINTER(I), P, ctypes.POINTER(D), P]
+    lib.lnocc_kpoint_df.restype = I
     lib.lnocc_debug_wait.argtypes = [I, ctypes.c_longlong, LL, P]
     lib.lnocc_debug_wait.restype = I
     lib.lnocc_workspace_bytes.argtypes = [I, I, I, ctypes.POINTER(Opts), LL]
@@ -424,6 +427,23 @@ def lnocc_active_space(precision, nocc, nvir, naux, eps, B, C_occ, C_vir, stream
     _check(load().lnocc_active_space(precision, nocc, nvir, naux, _ptr(eps), _ptr(B), no, _ptr(C_occ), nv,
                                      _ptr(C_vir), _ptr(eF), _ptr(BF), _ptr(CF), _stream(stream)))
     return eF, BF, CF
+
+
+def lnocc_kpoint_df(L, qneg, stream=None):
+    """Real DF factors B [nk * naux][n][n] (CUDA float64) of the q-sum of Eq. 27a from complex k-point factors
+    L [nk][naux][n][n] (CUDA complex128) and the -q index map qneg (sequence of nk ints).
+    Returns (B, relative symmetry error)."""
+    import torch
+    if not (isinstance(L, torch.Tensor) and L.is_cuda and L.dtype == torch.complex128 and L.is_contiguous()):
+        raise TypeError("L: expected a contiguous complex128 CUDA tensor")
+    nk, naux, n, n2 = (int(x) for x in L.shape)
+    if n2 != n or len(qneg) != nk:
+        raise ValueError("L must be [nk][naux][n][n] and qneg of length nk")
+    q = (ctypes.c_int * nk)(*[int(x) for x in qneg])
+    B = torch.empty(nk * naux, n, n, dtype=torch.float64, device=L.device)
+    err = ctypes.c_double(0.0)
+    _check(load().lnocc_kpoint_df(nk, naux, n, L.data_ptr(), q, _ptr(B), ctypes.byref(err), _stream(stream)))
+    return B, err.value
 
 
 def default_batch_opts(**kw) -> BatchOpts:

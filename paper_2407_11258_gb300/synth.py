@@ -250,11 +250,13 @@ def mlp_init(seed: int = 5100, hidden: int = 128) -> np.ndarray:
 def kpoint_factors(nk: int, naux: int, n: int, seed: int, decay: float = 20.0):
     """Stand-in for the k-point DF factors of the local Hamiltonian (Eq. 27b) on a 1-D mesh of nk
     momentum transfers q: real supercell factors B_R[P][p][r] (one block per cell R, symmetric in p, r,
-    drawn like df_tensor) and L^P_pr(q) = nk^(-1/2) sum_R exp(2 pi i q R / nk) B_R[P][p][r], which has the
+    drawn like df_tensor, scaled by nk^(-1/2)) and L^P_pr(q) = nk^(-1/2) sum_R exp(2 pi i q R / nk) B_R[P][p][r], which has the
     symmetries of real orbitals (L_pr(q) = L_rp(q), L(-q) = conj L(q)).
     Returns (L [nk][naux][n][n] complex128, qneg [nk] with qneg[q] = -q mod nk, B_cells [nk * naux][n][n])."""
     st = Stream(seed, 31)
-    cells = [df_tensor(st, naux, n, decay) for _ in range(nk)]
+    # each cell's factors drawn like df_tensor and scaled by nk^(-1/2): the supercell integrals then have
+    # the magnitude of nk * naux auxiliary functions drawn with N(0, 1 / (nk * naux)) entries
+    cells = [df_tensor(st, naux, n, decay) / np.sqrt(nk) for _ in range(nk)]
     Bc = np.stack(cells)                                    # [R][P][p][r]
     R = np.arange(nk)
     ph = np.exp(2j * np.pi * np.outer(R, R) / nk) / np.sqrt(nk)  # [q][R]
