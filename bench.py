@@ -510,6 +510,8 @@ def main():
     ap.add_argument("--fp64", action="store_true", help="case workload: plain FP64 path")
     ap.add_argument("--mlp-guess", action="store_true", help="case workload: also run the learned-guess kernel once")
     ap.add_argument("--tchunk", type=int, default=0, help="case workload: (T) W chunk bound in MB (0: library default)")
+    ap.add_argument("--tkernel", type=int, default=0,
+                    help="case workload: (T) contraction launches (0 auto, 1 one per term, 2 grouped)")
     ap.add_argument("--repeat", type=int, default=1, help="case workload: lnocc_triples calls (the last one is printed)")
     ap.add_argument("--ntrain", type=int, default=2000, help="mlp workload: training solves")
     ap.add_argument("--nheld", type=int, default=256, help="mlp workload: held-out fragments")
@@ -688,7 +690,8 @@ def run_case(args):
     eps, B, U = (torch.tensor(x, device="cuda") for x in (fr.eps, fr.B, fr.U_frag))
     prec = lnocc.LNOCC_PREC_FP64 if args.fp64 else lnocc.LNOCC_PREC_MIXED
     f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=prec, max_iter=args.iters,
-                                                                     triples_chunk_mb=args.tchunk))
+                                                                     triples_chunk_mb=args.tchunk,
+                                                                     triples_kernel=args.tkernel))
     t0 = time.perf_counter()
     e, it, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
     t1 = time.perf_counter()

@@ -50,6 +50,16 @@ extern "C" {
 #define LNOCC_GUESS_GIVEN 1 /* start from t1_in / t2_in (restart / checkpoint resume) */
 #define LNOCC_GUESS_MLP 2   /* t1 = 0, t2 = learned guess of the model attached by lnocc_frag_set_mlp */
 
+/* (T) contraction launches on the mixed path. PER_TERM: one launch per W term (sigma1 + sigma2, sigma3,
+ * sigma4, sigma6, sigma5) per chunk. GROUPED: two launches per chunk; the first runs sigma1 + sigma2,
+ * sigma3 and sigma5 of one (c, 128-row tile of (a, x)) block back to back in one CTA (the block stays
+ * in L2 between its store and its two reductions), the second sigma4 and sigma6. GROUPED needs
+ * nocc = 16 (one 256-column accumulator holds the (y, z) plane; 128 rows hold whole a values); AUTO
+ * takes it there and PER_TERM elsewhere, and GROUPED falls back to PER_TERM for other nocc. */
+#define LNOCC_TK_AUTO 0
+#define LNOCC_TK_PER_TERM 1
+#define LNOCC_TK_GROUPED 2
+
 #define LNOCC_FAULT_NAN_INPUT 1 /* fault injection (host side): poison one element of the B copy */
 #define LNOCC_FAULT_ZERO_DIIS 2 /* fault injection: run without DIIS extrapolation */
 
@@ -68,7 +78,9 @@ typedef struct lnocc_opts {
                          graph captured once per fragment (same kernels, same results; fewer host launches) */
   int triples_chunk_mb; /* bound on the W chunk of lnocc_triples in MB (0, the default: 768); part of the
                            workspace size that lnocc_workspace_bytes reports */
-  int reserved[4];
+  int triples_kernel;   /* (T) contraction launches on the mixed path: LNOCC_TK_AUTO (0, the default),
+                           LNOCC_TK_PER_TERM or LNOCC_TK_GROUPED (same W, same energy) */
+  int reserved[3];
 } lnocc_opts;
 
 typedef struct lnocc_info {

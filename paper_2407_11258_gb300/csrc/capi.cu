@@ -49,7 +49,7 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
   if (opts) o = *opts;
   if ((o.precision != LNOCC_PREC_FP64 && o.precision != LNOCC_PREC_MIXED) || o.max_iter < 0 || o.diis_space < 0 ||
       o.diis_space > 8 || o.n_refine < 0 || (o.graph != 0 && o.graph != 1) || !(o.conv_rms > 0) || !(o.conv_energy > 0) ||
-      o.triples_chunk_mb < 0) {
+      o.triples_chunk_mb < 0 || o.triples_kernel < LNOCC_TK_AUTO || o.triples_kernel > LNOCC_TK_GROUPED) {
     lnocc::set_error("lnocc_build_ints: bad options");
     return LNOCC_EINVAL;
   }

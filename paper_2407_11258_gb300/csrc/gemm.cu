@@ -471,7 +471,9 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   // epilogue scratch: the transpose tiles of 4 warps, or per warp BN column offsets + BN/4 flags
-  static constexpr int EPI_BYTES = 4 * 32 * 17 * 4 > 4 * (BN * 8 + BN / 4) ? 4 * 32 * 17 * 4 : 4 * (BN * 8 + BN / 4);
+  // (BN = 256, the grouped (T) launches: two 4 KB W boxes per warp)
+  static constexpr int EPI_BYTES0 = 4 * 32 * 17 * 4 > 4 * (BN * 8 + BN / 4) ? 4 * 32 * 17 * 4 : 4 * (BN * 8 + BN / 4);
+  static constexpr int EPI_BYTES = BN == 256 && EPI_BYTES0 < 32768 ? 32768 : EPI_BYTES0;
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 4 ? 4 : (192 * 1024) / STAGE_BYTES;
   static constexpr int ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two accumulators: MMA of tile t+1 overlaps epilogue of t
@@ -491,6 +493,8 @@ struct TcArgs {
   int* status;
   double* ws;
   const BatchEntry* batch;
+  GrpSpec g;              // grouped (T) launch when g.kind != 0 (tiles decoded from the spec)
+  OutMap Cg[3];           // output maps of the grouped launch's terms
 };
 
 // Per-tile problem description, computed identically by every role.
@@ -499,7 +503,64 @@ struct TileInfo {
   int m0, n0, z, M, kb0, nkbA;
   int a_row0, b_row0, a_row1, b_row1;
   long long cbase;
+  int nkb1, N;                 // second-segment K blocks and valid columns of this tile
+  int ma0, mb0, ma1, mb1;      // tensor maps (0..3 = tA0, tB0, tA1, tB1) of the two segments
+  int omap, cz;                // grouped launches: term (output map) and the region's W chunk c coordinate
 };
+
+// Grouped (T) launch: regions of one W chunk, each computed by one CTA as 3 (kind 1) or 2 (kind 2)
+// consecutive tiles that cover the same W elements; CTA b takes regions b, b + grid, ... Tile w of the
+// CTA's sequence is term w % terms of region blockIdx.x + (w / terms) * gridDim.x.
+//   kind 1 (maps: 0 = XT1 [A], 1 = TO [B], 2 = XT2 [A], 3 = TOT [B]); region (c, 128-row tile of (a, x)):
+//     term 0: sigma1 + sigma2 (store), term 1: sigma3, term 2: sigma5 (reductions)
+//   kind 2 (maps: 0 = TO [A], 1 = XT2 [B], 3 = XT1 [B]); region (128-row tile of (a, i, x), block of c):
+//     term 0: sigma4, term 1: sigma6 (reductions)
+// Every epilogue warp owns the same W elements in all terms of a region (its 32 rows are 2 whole a
+// values (kind 1) or 2 whole i values of one a (kind 2)), so the ordering of a region's store before
+// its reductions is the warp's own (a wait on its bulk groups), with no barrier across warps.
+__device__ __forceinline__ bool grp_tile(const GrpSpec& g, int w, TileInfo& ti) {
+  const int terms = g.kind == 1 ? 3 : 2;
+  const int r = blockIdx.x + (w / terms) * gridDim.x;
+  if (r >= g.nreg) return false;
+  const int term = w % terms;
+  ti.valid = true;
+  ti.n0 = 0;
+  ti.z = 0;
+  ti.kb0 = 0;
+  ti.nkbA = g.nkb;
+  ti.nkb1 = 0;
+  ti.omap = term;
+  ti.ma1 = 0;
+  ti.mb1 = 1;
+  ti.a_row1 = ti.b_row1 = 0;
+  if (g.kind == 1) {
+    const int cl = r / g.mt, c = g.c0 + cl;
+    ti.m0 = (r % g.mt) * 128;
+    ti.M = g.Ma;
+    ti.N = g.oo;
+    ti.cbase = cl * g.Sc;
+    ti.cz = cl;
+    if (term == 0) {
+      ti.ma0 = 0; ti.a_row0 = g.bvo;          ti.mb0 = 1; ti.b_row0 = c * g.oo;
+      ti.ma1 = 0; ti.a_row1 = c * g.vo;       ti.mb1 = 3; ti.b_row1 = g.b * g.oo;
+      ti.nkb1 = g.nkb;
+    } else if (term == 1) {
+      ti.ma0 = 2; ti.a_row0 = g.bvo;          ti.mb0 = 1; ti.b_row0 = c * g.oo;
+    } else {
+      ti.ma0 = 2; ti.a_row0 = c * g.vo;       ti.mb0 = 3; ti.b_row0 = g.b * g.oo;
+    }
+  } else {
+    const int cb = r / g.mt, cs = g.c0 + cb * g.cblk;
+    ti.m0 = (r % g.mt) * 128;
+    ti.M = g.Ma;
+    ti.N = min(g.cblk, g.c0 + g.nc - cs) * g.o;
+    ti.cbase = static_cast<long long>(cs - g.c0) * g.Sc;
+    ti.cz = cs - g.c0;
+    ti.ma0 = 0; ti.a_row0 = 0;
+    ti.mb0 = term == 0 ? 1 : 3; ti.b_row0 = g.bvo + cs * g.o;
+  }
+  return true;
+}
 
 template <int BN>
 __device__ __forceinline__ TileInfo tile_info(const TcArgs& p, int t) {
@@ -527,8 +588,124 @@ __device__ __forceinline__ TileInfo tile_info(const TcArgs& p, int t) {
     ti.kb0 = 0;
     ti.nkbA = p.nkb0;
   }
+  ti.nkb1 = p.nkb1;
+  ti.N = p.N;
+  ti.ma0 = 0;
+  ti.mb0 = 1;
+  ti.ma1 = 2;
+  ti.mb1 = 3;
+  ti.omap = 0;
+  ti.cz = 0;
   ti.valid = ti.m0 < ti.M && ti.nkbA + p.nkb1 > 0;
   return ti;
+}
+
+// Tile w of this CTA's sequence: 1 = a tile to process, 0 = an empty slot, -1 = the end.
+template <int BN>
+__device__ __forceinline__ int get_tile(const TcArgs& p, int w, TileInfo& ti) {
+  if (p.g.kind != 0) return grp_tile(p.g, w, ti) ? 1 : -1;
+  const int t = blockIdx.x + w * gridDim.x;
+  if (t >= p.tiles_m * p.tiles_n * p.tiles_z) return -1;
+  ti = tile_info<BN>(p, t);
+  return ti.valid ? 1 : 0;
+}
+
+__device__ __forceinline__ const CUtensorMap* pick_map(int id, const CUtensorMap* m0, const CUtensorMap* m1,
+                                                       const CUtensorMap* m2, const CUtensorMap* m3) {
+  return id == 0 ? m0 : id == 1 ? m1 : id == 2 ? m2 : m3;
+}
+
+// Epilogue of a grouped (T) tile (nocc = 16; W chunk viewed as the 5-D tensor {j, k, i, a, c}, j fastest).
+// This warp's 32 accumulator rows are sent 32 columns at a time: the 32 x 32 block is written into a
+// 4 KB shared box in W order (64-byte swizzle: byte x holds logical byte x ^ (((x >> 7) & 3) << 4)) and
+// one lane issues a TMA store (term 0 of kind 1) or a TMA reduce-add (every other term) of the box.
+// Two boxes per warp alternate; a box is rewritten once the copy issued from it two steps before has
+// read it. Boxes (j, k, i, a, c) and the thread -> element maps (row r = 16 hi + lo, column n):
+//   kind 1, term 0 (sigma1 + sigma2): rows (a, i), cols (k, j); box {16, 2, 16, 2, 1} at (0, 2cc, 0, a0, c)
+//   kind 1, term 1 (sigma3):          rows (a, j), cols (k, i); the same box
+//   kind 1, term 2 (sigma5):          rows (a, k), cols (i, j); box {16, 16, 2, 2, 1} at (0, 0, 2cc, a0, c)
+//   kind 2, term 0 (sigma4):          rows (a, i, k), cols (c, j); box {16, 16, 2, 1, 2} at (0, 0, i0, a0, c + 2cc)
+//   kind 2, term 1 (sigma6):          rows (a, i, j), cols (c, k); the same box
+template <int BN>
+__device__ __forceinline__ void grp_epilogue(const TcArgs& p, const TileInfo& ti, const CUtensorMap* tW0,
+                                             const CUtensorMap* tW1, uint32_t acc, uint32_t sbox, int ew, int lane,
+                                             int& nbox) {
+  constexpr int O = 16;
+  const GrpSpec& g = p.g;
+  const int term = ti.omap;
+  const int mb = ti.m0 + ew * 32;  // first accumulator row of this warp
+  const int hi = lane >> 4, lo = lane & 15;
+  const int a0 = g.kind == 1 ? mb / O : mb / (O * O);
+  const int i0 = g.kind == 1 ? 0 : (mb / O) % O;
+  if (a0 > g.b) return;  // rows past the slab (a > b): nothing to write
+  const bool vec = (g.kind == 1 && term != 1) || (g.kind == 2 && term == 0);
+  // per-thread swizzle terms: 16-byte chunk t of a 64-byte row, or word j of it
+  const int x = vec ? (g.kind == 1 && term == 0 ? lane & 3 : (lo >> 1) & 3) : 0;
+  uint32_t off4[4], jx[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    off4[t] = static_cast<uint32_t>((t ^ x) << 4);
+    jx[t] = static_cast<uint32_t>(4 * (lo ^ (t << 2)));
+  }
+#pragma unroll 1
+  for (int cc = 0; cc < BN / 32; ++cc) {
+    if (g.kind == 2 && ti.cz + 2 * cc >= g.nc) break;  // c past the chunk: the rest of the block is empty
+    float v[32];
+    tmem_ld32(acc + cc * 32, v);
+    const uint32_t buf = sbox + (nbox & 1) * 4096;
+    if (lane == 0) bulk_wait_read1();
+    __syncwarp();
+    if (g.kind == 1 && term == 0) {
+      const uint32_t base = buf + lane * 128;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        st_shared_v4(base + (q >> 2) * 64 + off4[q & 3], v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (g.kind == 1 && term == 1) {
+      const uint32_t base = buf + hi * 2048;
+#pragma unroll
+      for (int col = 0; col < 32; ++col) {
+        const int kp = col >> 4, i = col & 15;
+        st_shared_f32(base + i * 128 + kp * 64 + jx[i & 3], v[col]);
+      }
+    } else if (vec) {
+      // kind 1 term 2: thread (a', k), columns (i', j); kind 2 term 0: thread (i', k), columns (c', j)
+      const uint32_t base = buf + (g.kind == 1 ? hi * 2048 : hi * 1024) + lo * 64;
+      const uint32_t step = g.kind == 1 ? 1024 : 2048;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          st_shared_v4(base + h * step + off4[q], v[16 * h + 4 * q], v[16 * h + 4 * q + 1], v[16 * h + 4 * q + 2],
+                       v[16 * h + 4 * q + 3]);
+    } else {
+      // kind 2 term 1: thread (i', j), columns (c', k)
+      const uint32_t base = buf + hi * 1024;
+#pragma unroll
+      for (int col = 0; col < 32; ++col) {
+        const int cp = col >> 4, k = col & 15;
+        st_shared_f32(base + cp * 2048 + k * 64 + jx[(k >> 1) & 3], v[col]);
+      }
+    }
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+      if (g.kind == 1) {
+        if (term == 0) {
+          tma_store_5d(tW0, buf, 0, 2 * cc, 0, a0, ti.cz);
+        } else {
+          if (term == 1 && cc == 0) bulk_wait_all();  // the region's stores are performed first
+          if (term == 1)
+            tma_reduce_add_5d(tW0, buf, 0, 2 * cc, 0, a0, ti.cz);
+          else
+            tma_reduce_add_5d(tW1, buf, 0, 0, 2 * cc, a0, ti.cz);
+        }
+      } else {
+        tma_reduce_add_5d(tW0, buf, 0, 0, i0, a0, ti.cz + 2 * cc);
+      }
+      bulk_commit();
+    }
+    ++nbox;
+  }
 }
 
 // Persistent warp-specialized GEMM: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
@@ -536,7 +713,8 @@ __device__ __forceinline__ TileInfo tile_info(const TcArgs& p, int t) {
 template <int BN>
 __global__ void __launch_bounds__(256, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tB0,
-              const __grid_constant__ CUtensorMap tA1, const __grid_constant__ CUtensorMap tB1, const TcArgs p) {
+              const __grid_constant__ CUtensorMap tA1, const __grid_constant__ CUtensorMap tB1,
+              const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUtensorMap tW1, const TcArgs p) {
   using Cfg = TcCfg<BN>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -549,7 +727,6 @@ __global__ void __launch_bounds__(256, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int ntiles = p.tiles_m * p.tiles_n * p.tiles_z;
   const OutMap& C = p.C;
 
   if (threadIdx.x == 0) {
@@ -564,7 +741,7 @@ __global__ void __launch_bounds__(256, 1)
     fence_barrier_init();
     prefetch_tensormap(&tA0);
     prefetch_tensormap(&tB0);
-    if (p.nkb1 > 0) {
+    if (p.nkb1 > 0 || p.g.kind != 0) {
       prefetch_tensormap(&tA1);
       prefetch_tensormap(&tB1);
     }
@@ -579,10 +756,12 @@ __global__ void __launch_bounds__(256, 1)
     // ---------------- TMA producer
     int g = 0;  // global K-block counter across tiles (stage / phase)
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const TileInfo ti = tile_info<BN>(p, t);
-      if (!ti.valid) continue;
-      const int nkb = ti.nkbA + p.nkb1;
+    for (int w = 0; ok; ++w) {
+      TileInfo ti;
+      const int gt = get_tile<BN>(p, w, ti);
+      if (gt < 0) break;
+      if (gt == 0) continue;
+      const int nkb = ti.nkbA + ti.nkb1;
       for (int kb = 0; kb < nkb; ++kb, ++g) {
         const int s = g % S;
         if (g >= S && !mbar_wait(&empty[s], ((g / S) - 1) & 1)) {
@@ -593,8 +772,8 @@ __global__ void __launch_bounds__(256, 1)
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
         mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
         const bool seg0 = kb < ti.nkbA;
-        const CUtensorMap* ta = seg0 ? &tA0 : &tA1;
-        const CUtensorMap* tb = seg0 ? &tB0 : &tB1;
+        const CUtensorMap* ta = pick_map(seg0 ? ti.ma0 : ti.ma1, &tA0, &tB0, &tA1, &tB1);
+        const CUtensorMap* tb = pick_map(seg0 ? ti.mb0 : ti.mb1, &tA0, &tB0, &tA1, &tB1);
         const int kc = (seg0 ? ti.kb0 + kb : kb - ti.nkbA) * Cfg::BK;
         const int ar = (seg0 ? ti.a_row0 : ti.a_row1) + ti.m0, br = (seg0 ? ti.b_row0 : ti.b_row1) + ti.n0;
         tma_load_3d(st, ta, &full[s], kc, ar, 0);
@@ -610,9 +789,11 @@ __global__ void __launch_bounds__(256, 1)
     constexpr uint32_t idesc = idesc_bf16_f32(Cfg::BM, BN);
     int g = 0, it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const TileInfo ti = tile_info<BN>(p, t);
-      if (!ti.valid) continue;
+    for (int w = 0; ok; ++w) {
+      TileInfo ti;
+      const int gt = get_tile<BN>(p, w, ti);
+      if (gt < 0) break;
+      if (gt == 0) continue;
       const int buf = it & 1;
       if (it >= 2 && !mbar_wait(&acce[buf], ((it / 2) - 1) & 1)) {
         atomicExch(p.status, kDevTimeoutMma);
@@ -620,7 +801,7 @@ __global__ void __launch_bounds__(256, 1)
       }
       tc_fence_after();
       const uint32_t acc = tmem + buf * Cfg::ACC_COLS;
-      const int nkb = ti.nkbA + p.nkb1;
+      const int nkb = ti.nkbA + ti.nkb1;
       for (int kb = 0; kb < nkb; ++kb, ++g) {
         const int s = g % S;
         if (!mbar_wait(&full[s], (g / S) & 1)) {
@@ -654,10 +835,12 @@ __global__ void __launch_bounds__(256, 1)
     // FP32 destination with beta 0 or 1: direct row writes with per-tile column offsets (below)
     const bool f32_direct = !p.ws && C.dst32 && (p.beta_f == 1.f || p.beta_f == 0.f);
     float* tile = epi + ew * (32 * 17);
-    int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const TileInfo ti = tile_info<BN>(p, t);
-      if (!ti.valid) continue;
+    int it = 0, nbox = 0;
+    for (int w = 0;; ++w) {
+      TileInfo ti;
+      const int gt = get_tile<BN>(p, w, ti);
+      if (gt < 0) break;
+      if (gt == 0) continue;
       const int buf = it & 1;
       if (!mbar_wait(&accf[buf], (it / 2) & 1)) {
         if (lane == 0) atomicExch(p.status, kDevTimeoutEpilogue);
@@ -666,7 +849,12 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const uint32_t acc = tmem + buf * Cfg::ACC_COLS + (static_cast<uint32_t>(ew * 32) << 16);
       const int M = ti.M;
-      if (f32_direct) {
+      const bool grp = p.g.kind != 0;
+      const OutMap& C = grp ? p.Cg[ti.omap] : p.C;
+      if (grp) {
+        // W boxes: 2 x 4 KB per epilogue warp in the epilogue scratch (1024-byte aligned)
+        grp_epilogue<BN>(p, ti, &tW0, &tW1, acc, smem_u32(epi) + ew * 8192, ew, lane, nbox);
+      } else if (f32_direct) {
         // FP32 destination, beta 0 or 1 (the (T) W terms). Each epilogue warp computes the column
         // offsets of the tile once into its own shared-memory slot, with a flag per group of 4 columns
         // that are consecutive and 16-byte aligned in the destination (warp-local: no barrier across
@@ -681,7 +869,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int n = ti.n0 + 4 * q + k;
-            co[k] = n < p.N ? out_noff(C, n) : -1;
+            co[k] = n < ti.N ? out_noff(C, n) : -1;
             colo[4 * q + k] = co[k];
           }
           qok[q] = co[0] >= 0 && co[3] >= 0 && co[1] == co[0] + 1 && co[2] == co[0] + 2 && co[3] == co[0] + 3 &&
@@ -693,8 +881,8 @@ __global__ void __launch_bounds__(256, 1)
         const long long rowoff = mvalid ? ti.cbase + out_moff(C, m) : 0;
         float* rowp = C.dst32 + rowoff;
         const bool rowv4 = mvalid && (reinterpret_cast<uintptr_t>(rowp) & 15) == 0;
-        const float al = p.alpha_f;
-        const bool acc_mode = p.beta_f == 1.f;
+        const float al = grp ? static_cast<float>(C.alpha) : p.alpha_f;
+        const bool acc_mode = (grp ? static_cast<float>(C.beta) : p.beta_f) == 1.f;
         // 16 accumulator columns starting at c0 (values v) to the destination row
         auto emit16 = [&](const float* v, int c0) {
 #pragma unroll
@@ -816,6 +1004,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_arrive(&acce[buf]);
       ++it;
     }
+    if (p.g.kind != 0 && lane == 0) bulk_wait_all();  // W boxes read and written before the CTA retires
   }
   tc_fence_before();
   __syncthreads();
@@ -907,7 +1096,7 @@ static void launch_tc(const Packed& A0, const Packed& B0, const Packed* A1, cons
   const long long ntiles = static_cast<long long>(args.tiles_m) * args.tiles_n * args.tiles_z;
   const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   count_launch();
-  k_gemm_tc<BN><<<grid, 256, Cfg::SMEM, s>>>(ta0, tb0, ta1, tb1, args);
+  k_gemm_tc<BN><<<grid, 256, Cfg::SMEM, s>>>(ta0, tb0, ta1, tb1, ta0, ta0, args);
   if (splits > 1) splitk_reduce(splits, args.M, args.N, args.C, s);
 }
 
@@ -1116,6 +1305,65 @@ static TcArgs tc_args(int M, int N, int nkb0, int nkb1, const OutMap& C, int* ds
   a.C = C;
   a.status = dstatus;
   return a;
+}
+
+// The FP32 W chunk [c][a][i][k][j] (nocc = 16) as the 5-D tensor {j, k, i, a, c}; 64-byte swizzled boxes.
+static bool make_wmap(CUtensorMap* map, float* W, const GrpSpec& g, const cuuint32_t box[5]) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[5] = {16, 16, 16, static_cast<cuuint64_t>(g.b + 1), static_cast<cuuint64_t>(g.nc)};
+  cuuint64_t strides[4] = {16 * 4, 256 * 4, 4096 * 4, static_cast<cuuint64_t>(g.Sc) * 4};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSpec& g, const OutMap* Cg, int ncg,
+                  cudaStream_t s, int* dstatus) {
+  if (g.nreg <= 0) return;
+  if (g.o != 16 || g.oo != 256 || (g.kind != 1 && g.kind != 2) || !Cg[0].dst32) {
+    set_error("gemm_grouped: nocc 16 and an FP32 W chunk only");
+    return;
+  }
+  using Cfg = TcCfg<256>;
+  static_assert(Cfg::SMEM <= 232448, "shared memory of the 256-column configuration");
+  set_smem_attr<256>();
+  CUtensorMap m[4];
+  for (int k = 0; k < 4; ++k) {
+    if (!make_map(&m[k], *ops[k], box_rows[k])) {
+      set_error("cuTensorMapEncodeTiled failed");
+      return;
+    }
+  }
+  CUtensorMap w0, w1;
+  const cuuint32_t box_a0[5] = {16, 2, 16, 2, 1}, box_a1[5] = {16, 16, 2, 2, 1}, box_b[5] = {16, 16, 2, 1, 2};
+  if (!make_wmap(&w0, Cg[0].dst32, g, g.kind == 1 ? box_a0 : box_b) ||
+      !make_wmap(&w1, Cg[0].dst32, g, g.kind == 1 ? box_a1 : box_b)) {
+    set_error("cuTensorMapEncodeTiled failed (W chunk)");
+    return;
+  }
+  TcArgs a{};
+  a.M = g.Ma;
+  a.N = 256;
+  a.nkb0 = g.nkb;
+  a.kb_per = g.nkb;
+  a.tiles_m = a.tiles_n = a.tiles_z = 1;
+  a.status = dstatus;
+  a.g = g;
+  for (int k = 0; k < ncg && k < 3; ++k) a.Cg[k] = Cg[k];
+  a.C = Cg[0];
+  a.alpha_f = 1.f;
+  a.beta_f = 0.f;
+  GemmStats& st = gemm_stats();
+  st.launches++;
+  // useful flops: kind 1 = sigma1, sigma2, sigma3, sigma5 over (a, x) x (y, z) per c; kind 2 = sigma4,
+  // sigma6 over (a, x, y) x (c, z)
+  st.flops += g.kind == 1 ? 2.0 * g.Ma * g.oo * (64.0 * g.nkb) * 4 * g.nc
+                          : 2.0 * g.Ma * (1.0 * g.nc * g.o) * (64.0 * g.nkb) * 2;
+  const int grid = static_cast<int>(std::min<long long>(g.nreg, num_sms()));
+  count_launch();
+  k_gemm_tc<256><<<grid, 256, Cfg::SMEM, s>>>(m[0], m[1], m[2], m[3], w0, w1, a);
 }
 
 void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,

@@ -101,6 +101,24 @@ void gemm2_off(const Packed& A0, int a0, const Packed& B0, int b0, int K0, const
 void gemm(const Packed& A, const Packed& B, int M, int N, int K, const OutMap& C, cudaStream_t s,
           int* dstatus);
 
+// A grouped (T) launch (see grp_tile in gemm.cu): kind 1 = sigma1 + sigma2, sigma3, sigma5 per region
+// (c, 128-row tile of (a, x)); kind 2 = sigma4, sigma6 per region (128-row tile of (a, i, x), block of
+// cblk c values). Rows: A operands start at the given bases; W chunk offsets advance by Sc per c.
+struct GrpSpec {
+  int kind;          // 0: not a grouped launch
+  int nreg;          // regions
+  int mt;            // 128-row tiles per c (kind 1) or per c block (kind 2)
+  int Ma;            // valid rows of the problem: (b + 1) o (kind 1) or (b + 1) o^2 (kind 2)
+  int nkb;           // K blocks of one term (Kp / 64)
+  int c0, nc, cblk;  // the chunk's first c, its number of c, c values per column block (kind 2)
+  int b, bvo, vo, oo, o;  // slab b, b v o, v o, o^2, o
+  long long Sc;      // W elements per c in the chunk
+};
+// Grouped (T) contraction on BF16 hi/lo operands ops[0..3] (box rows 128 for A roles, 256 for B roles)
+// with output maps Cg[0..ncg) (alpha 1; beta 0 for the first term of a region, 1 for the others).
+void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSpec& g, const OutMap* Cg, int ncg,
+                  cudaStream_t s, int* dstatus);
+
 // Workspace for split-K partials (FP64 elements), provided by the caller of the contraction engine.
 // Per host thread: each thread drives its own fragment and stream.
 struct SplitWs {

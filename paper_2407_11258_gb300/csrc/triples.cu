@@ -239,7 +239,8 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
       dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
     act[pi] = !dup;
   }
-  Real r_can = 0, r_frag = 0;  // per-thread partials (converted to FP64 for the block sum)
+  // per-thread partials in FP64: FP32 (Real = float) sums run over one (j, k) only (6 nocc terms)
+  double r_can = 0, r_frag = 0;
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
     int off[6], si[6];
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
     act[pi] = !dup;
   }
   constexpr int NL = NLO > 0 ? NLO : 1;
-  float r_can = 0.f, r_frag = 0.f;
+  double r_can = 0, r_frag = 0;  // FP32 sums run over one (j, k) only; partials across (j, k) in FP64
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
     int off[6], si[6];
@@ -464,13 +465,15 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
         for (int al = 0; al < NLO; ++al) zy[pi][al] = __ffma2_rn(u2[al], zyv, zy[pi][al]);
       }
     }
-    r_can += acc;
+    r_can += static_cast<double>(acc);
+    float f = 0.f;
 #pragma unroll
     for (int pi = 0; pi < 6; ++pi)
 #pragma unroll
-      for (int al = 0; al < NLO; ++al) r_frag += zy[pi][al].x * zy[pi][al].y;
+      for (int al = 0; al < NLO; ++al) f += zy[pi][al].x * zy[pi][al].y;
+    r_frag += static_cast<double>(f);
   }
-  double e_can = static_cast<double>(r_can), e_frag = static_cast<double>(r_frag);
+  double e_can = r_can, e_frag = r_frag;
   __shared__ double sh[2][32];
   for (int off = 16; off > 0; off >>= 1) {
     e_can += __shfl_xor_sync(0xffffffffu, e_can, off);
@@ -840,6 +843,12 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     return m;
   };
   const int o2 = static_cast<int>(oo);
+  // grouped launches (two per chunk instead of five) where one accumulator holds a (y, z) plane and
+  // 128-row tiles hold whole a values
+  const bool grouped = bf && o == 16 && opts.triples_kernel != LNOCC_TK_PER_TERM;
+  const Packed* ops_a[4] = {&XT1, &TO, &XT2, &TOT};
+  const Packed* ops_b[4] = {&TO, &XT2, &TO, &XT1};
+  const int box_ab[4] = {128, 256, 128, 256};
   // tuning passes (t_max_chunks > 0) visit about t_max_chunks chunks spread over the plan
   const size_t chunk_stride = t_max_chunks > 0 ? std::max<size_t>(1, plan.size() / t_max_chunks) : 1;
   size_t chunk_idx = 0;
@@ -854,6 +863,42 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     // W layout [c - c0][a][i][k][j]; each term is one contraction over K = v + o (d-part, then l-part).
+    if (grouped) {
+      // launch 1, per (c, 128-row tile of (a, x)): sigma1 + sigma2 stored, then sigma3 and sigma5 added
+      // (the output maps of the per-term launches below, restricted to one c)
+      GrpSpec g{};
+      g.kind = 1;
+      g.Ma = Ma;
+      g.mt = (Ma + 127) / 128;
+      g.nkb = XT1.Kp / 64;
+      g.c0 = c0;
+      g.nc = nc;
+      g.cblk = 256 / o;
+      g.b = b;
+      g.bvo = xb;
+      g.vo = v * o;
+      g.oo = o2;
+      g.o = o;
+      g.Sc = Sc;
+      g.nreg = nc * g.mt;
+      OutMap ca[3] = {omap(0.0), omap(1.0), omap(1.0)};
+      ca[0].sm1 = ooo; ca[0].sm0 = oo; ca[0].mdiv = o; ca[0].sn1 = o; ca[0].sn0 = 1; ca[0].ndiv = o;   // (a,i) x (k,j)
+      ca[1].sm1 = ooo; ca[1].sm0 = 1; ca[1].mdiv = o; ca[1].sn1 = o; ca[1].sn0 = oo; ca[1].ndiv = o;   // (a,j) x (k,i)
+      ca[2].sm1 = ooo; ca[2].sm0 = o; ca[2].mdiv = o; ca[2].sn1 = oo; ca[2].sn0 = 1; ca[2].ndiv = o;   // (a,k) x (i,j)
+      gemm_grouped(ops_a, box_ab, g, ca, 3, s, dstatus);
+      // launch 2, per (128-row tile of (a, x, y), block of 256 / o values of c): sigma4 and sigma6 added
+      GrpSpec h = g;
+      h.kind = 2;
+      h.Ma = Ma2;
+      h.mt = (Ma2 + 127) / 128;
+      h.nreg = h.mt * ((nc + g.cblk - 1) / g.cblk);
+      OutMap cb[2] = {omap(1.0), omap(1.0)};
+      cb[0].sm2 = ooo; cb[0].sm1 = oo; cb[0].sm0 = o; cb[0].mdiv = o; cb[0].mdiv1 = o;   // (a,i,k) x (c,j)
+      cb[0].sn1 = Sc; cb[0].sn0 = 1; cb[0].ndiv = o;
+      cb[1].sm2 = ooo; cb[1].sm1 = oo; cb[1].sm0 = 1; cb[1].mdiv = o; cb[1].mdiv1 = o;   // (a,i,j) x (c,k)
+      cb[1].sn1 = Sc; cb[1].sn0 = o; cb[1].ndiv = o;
+      gemm_grouped(ops_b, box_ab, h, cb, 2, s, dstatus);
+    } else {
     // sigma1 + sigma2 (batched over c, two K segments into one accumulator; first writer of W):
     // rows (a,i), cols (k,j): (ai|bd) t_kj^cd - t_il^ab (ck|jl) + (ai|cd) t_jk^bd - t_il^ac (bj|kl)
     {
@@ -890,6 +935,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       m.sm1 = ooo; m.sm0 = o; m.mdiv = o;
       m.sn1 = oo; m.sn0 = 1; m.ndiv = o;
       gemm_batched(XT2, TOT, dbat + ch.tab, nc, Ma, o2, Kt, m, s, dstatus);
+    }
     }
     cudaEventRecord(e1, s);
     gev.emplace_back(e0, e1);

@@ -16,6 +16,7 @@ LNOCC_OK, LNOCC_EINVAL, LNOCC_ENOMEM, LNOCC_ENOCONV, LNOCC_ENUMERIC, LNOCC_ETIME
 LNOCC_PREC_FP64, LNOCC_PREC_MIXED = 0, 1
 LNOCC_GUESS_MP2, LNOCC_GUESS_GIVEN, LNOCC_GUESS_MLP = 0, 1, 2
 LNOCC_FAULT_NAN_INPUT, LNOCC_FAULT_ZERO_DIIS = 1, 2
+LNOCC_TK_AUTO, LNOCC_TK_PER_TERM, LNOCC_TK_GROUPED = 0, 1, 2
 
 ERR_NAMES = {0: "LNOCC_OK", 1: "LNOCC_EINVAL", 2: "LNOCC_ENOMEM", 3: "LNOCC_ENOCONV", 4: "LNOCC_ENUMERIC",
              5: "LNOCC_ETIMEOUT", 6: "LNOCC_ECUDA"}
@@ -39,7 +40,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("diis_space", ctypes.c_int),
                 ("n_refine", ctypes.c_int), ("conv_rms", ctypes.c_double), ("conv_energy", ctypes.c_double),
                 ("fault_inject", ctypes.c_int), ("verbose", ctypes.c_int), ("graph", ctypes.c_int),
-                ("triples_chunk_mb", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("triples_chunk_mb", ctypes.c_int), ("triples_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Info(ctypes.Structure):

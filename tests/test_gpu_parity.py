@@ -153,6 +153,38 @@ def test_half_diamond_with_triples(lnocc):
         assert_parity(gpu_solve(lnocc, fr, prec), ref, tol)
 
 
+def test_half_lithium_small_gap_with_triples(lnocc):
+    """Lithium-like small-gap energies (HOMO-LUMO gap 0.040 Eh, the smallest of the lithium-like range)
+    at the half-diamond sizes, with (T): both paths against the stored oracle energies. The oracle's
+    CCSD energy settles to a spread of 4.5e-10 Eh over its last 20 iterations (its amplitude change
+    stays near 1e-9 there), so the FP64 path is held to 2e-9 Eh here instead of 1e-9."""
+    ref = golden("oracle_half_lithium.json")["half_lithium"]
+    fr = synth.make_fragment(16, 120, 480, 2505, decay=20.0, small_gap=True, frag=(0, 1))
+    assert (fr.nocc, fr.nvir, fr.naux, fr.seed) == (ref["nocc"], ref["nvir"], ref["naux"], ref["seed"])
+    assert abs(float(fr.eps[16] - fr.eps[15]) - ref["gap"]) < 1e-15
+    for prec, tol in ((1, MIXED_TOL), (0, 2e-9)):
+        assert_parity(gpu_solve(lnocc, fr, prec, max_iter=300), ref, tol)
+
+
+def test_triples_grouped_launches(lnocc):
+    """nocc=16 runs the (T) contractions as two grouped launches per W chunk (sigma1 + sigma2, sigma3,
+    sigma5 per (c, row tile); sigma4, sigma6 per (row tile, block of 16 c)). Both launch forms against
+    the live oracle, with the default chunk (one per b-slab) and with 1 MB chunks, which split slabs
+    into several chunks and leave partial c blocks."""
+    fr = synth.make_fragment(16, 40, 160, 1640, decay=20.0, frag=(0, 1))
+    ref = oracle_solve(fr)
+    res = {}
+    for tk in (lnocc.LNOCC_TK_PER_TERM, lnocc.LNOCC_TK_GROUPED):
+        for mb in (0, 1):
+            got = gpu_solve(lnocc, fr, 1, triples_kernel=tk, triples_chunk_mb=mb)
+            assert_parity(got, ref, MIXED_TOL)
+            res[tk, mb] = got
+    # the same FP32 products summed in another order: far inside the mixed tolerance of each other
+    for mb in (0, 1):
+        for k in ("e_t", "e_t_frag"):
+            assert abs(res[1, mb][k] - res[2, mb][k]) < 1e-9, (mb, k)
+
+
 # ------------------------------------------------------------------ properties
 
 def test_deterministic_repeat(lnocc):
