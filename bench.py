@@ -68,6 +68,39 @@ def read_peaks():
     return 1900.0, 1700.0, 6800.0, "fallback"
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_gemm_tc_triples_traffic_nocc16_nvir240.md")
+TRAFFIC_SOURCES = ("paper_2407_11258_gb300/csrc/gemm.cu", "paper_2407_11258_gb300/csrc/triples.cu")
+
+
+def sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes (read + write) of the (T) contraction launches of one lnocc_triples call, from the ncu
+    summary under profiles/, or None when the kernel sources have changed since that capture (the summary
+    records a digest of them)."""
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None, "no capture"
+    rec = {}
+    for line in open(TRAFFIC_PROFILE):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            rec[k.strip()] = v.strip().strip("`")
+    try:
+        tb, dig = float(rec["traffic_bytes_per_call"]), rec["sources_sha256_16"]
+    except (KeyError, ValueError):
+        return None, "capture summary unreadable"
+    if dig != sources_digest():
+        return None, "kernel sources changed since the capture"
+    return tb, os.path.relpath(TRAFFIC_PROFILE, ROOT)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
 
@@ -598,6 +631,7 @@ def main():
     alg = triples_algorithmic_flops(o, v)
     achieved = alg / (gemm_ms * 1e-3) / 1e12
     peak = peak_burst / 3.0  # BF16x3: three bf16 products per useful product
+    traffic, traffic_src = recorded_traffic()
     out = {
         "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -615,7 +649,8 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 6 * 8},
         "gpu_launches": launches,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "traffic_unit": "DRAM bytes read + written by the k_gemm_tc launches of one lnocc_triples call",
                      "kernel": "k_gemm_tc ((T) W contractions)",
                      "note": f"useful (T) contraction flops 2o^3v^4+2o^4v^3 per call / event time of those launches; "
                              f"peak = {peak_src} bf16 burst {peak_burst} / 3 (BF16x3)",

@@ -69,7 +69,12 @@ typedef struct lnocc_opts {
   int precision;      /* LNOCC_PREC_FP64 or LNOCC_PREC_MIXED */
   int max_iter;       /* CCSD iteration cap (default 100) */
   int diis_space;     /* Pulay DIIS vectors, 0..8 (default 8) */
-  int n_refine;       /* mixed only: CCSD iterations with an FP64 residual after mixed convergence */
+  int n_refine;       /* mixed only: at most this many FP64-residual CCSD iterations, run only when the
+                         mixed solve reaches its noise floor with an energy spread above 1e-7 Eh (they
+                         continue from the lowest-rms amplitudes until rms < conv_rms and
+                         |dE| < max(conv_energy, 1e-8) Eh); 0 (default):
+                         such a solve returns LNOCC_ENOCONV with the energy of those amplitudes. Needs
+                         the FP64 operands, built by lnocc_build_ints when n_refine > 0 */
   double conv_rms;    /* convergence: rms of the doubles update |R/D| below this (default 1e-8) */
   double conv_energy; /* convergence: |E_k - E_k-1| below this (default 1e-10 Eh) */
   int fault_inject;   /* LNOCC_FAULT_* bitmask, 0 in production */
@@ -99,6 +104,10 @@ typedef struct lnocc_info {
   double t_triples_gemm_ms;  /* last lnocc_triples: device time of its contraction launches (CUDA events) */
   double t_triples_ms;       /* last lnocc_triples: device time of the whole call (CUDA events) */
   long long device_allocs;   /* library-wide count of device allocations made so far (monotonic) */
+  double floor_spread;       /* mixed: CCSD energy spread (Eh) over the last iterations when the noise floor
+                                was reached (0 if the FP64 thresholds were met first) */
+  int n_refined;             /* mixed: FP64-residual iterations the last solve ran (see opts.n_refine) */
+  int diis_restarts;         /* mixed: DIIS subspace restarts from the lowest-rms amplitudes */
 } lnocc_info;
 
 /* Fill `opts` with the defaults listed above (precision = LNOCC_PREC_MIXED). */

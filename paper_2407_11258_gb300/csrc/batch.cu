@@ -58,7 +58,7 @@ long long estimate_fragment_bytes(int o_, int v_, int N_, bool mixed, int n_refi
   const long long np_v = v * (v + 1) / 2, nm_v = std::max(1LL, v * (v - 1) / 2);
   long long b = 0;
   b += 8 * (n + N * oo + 2 * N * ov + 2 * N * vv + 6 * n * n + 2 * ov * ov + N);
-  b += 8 * (3 * L + 8 * oo * vv + 2 * oo * ov + 2 * oo * oo + N * ov + ov + vv + 2 * oo);
+  b += 8 * ((mixed ? 4 : 3) * L + 8 * oo * vv + 2 * oo * ov + 2 * oo * oo + N * ov + ov + vv + 2 * oo);
   b += 8 * (np_v * np_o + nm_v * nm_o + N * ov);
   b += 8 * 2 * std::min(diis, 8) * L;
   const long long cap = packing_scratch_elems(o_, v_, N_);

@@ -181,6 +181,9 @@ int lnocc_frag_info(const lnocc_frag* h, lnocc_info* info) {
   info->t_triples_gemm_ms = f.t_gemm_ms;
   info->t_triples_ms = f.t_triples_ms;
   info->device_allocs = lnocc::alloc_counter().load();
+  info->floor_spread = f.floor_spread;
+  info->n_refined = f.n_refined;
+  info->diis_restarts = f.diis_restarts;
   return LNOCC_OK;
 }
 

@@ -31,7 +31,7 @@ struct Consts {
 
 // Sizes (bytes) of the device temporaries of one lnocc_triples call (triples.cu).
 struct TriplesPlan {
-  size_t xt, to, ovoo, pbvv, ovvv_chunk, w, tpart, batch, u, total;
+  size_t xt, to, ovoo, pbvv, ovvv_chunk, w, tpart, batch, u, ovt, total;
   long long welems, nblk;
   int bc;
 };
@@ -71,6 +71,7 @@ struct Frag {
 
   // amplitudes: x = [t1 (o*v) | t2 (o*o*v*v)]
   double *xcur = nullptr, *xnew = nullptr, *enew = nullptr;
+  double* xbest = nullptr;  // mixed: amplitudes of the lowest-rms iteration
   // per-iteration work
   double *Boo_h = nullptr, *Bvo_h = nullptr, *Bvv_h = nullptr;
   double *Xm = nullptr, *Ym = nullptr, *hh = nullptr, *tmpn = nullptr, *Fh = nullptr, *xq = nullptr;
@@ -100,6 +101,8 @@ struct Frag {
 
   // results
   double e_mp2 = 0.0, e_ccsd = 0.0, last_rms = 0.0;
+  double floor_spread = 0.0;  // mixed: energy spread over the window at the noise floor
+  int n_refined = 0, diis_restarts = 0;
   int n_iter = 0;
   bool converged = false, have_amps = false;
   double flops_t = 0.0;

@@ -331,9 +331,9 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
 //  * the projected i-sums of z and y for one LO form a pair updated by one packed FP32 FMA, with
 //    U[i][alpha] duplicated into both halves of a pair in shared memory.
 template <int NLO>
-__global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ W, long long slot_stride, int b, int c0,
+__global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2) k_t_energy_f32(const float* __restrict__ W, long long slot_stride, int b, int c0,
                                                       int o, int v, const double* __restrict__ eps,
-                                                      const double* __restrict__ t1, const double* __restrict__ ovov,
+                                                      const double* __restrict__ t1, const float* __restrict__ ovT,
                                                       const double* __restrict__ U, double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int slot = blockIdx.y, a = blockIdx.x;
@@ -355,13 +355,16 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
   // U pairs (U[i][al], U[i][al]), 16-byte aligned for 128-bit loads
   const int uoff = (2 * blk + 3 * o2p + 4 * o + 3) & ~3;
   float* U2 = reinterpret_cast<float*>(smraw) + uoff;
-  const long long ov = 1LL * o * v;
   const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
+  // (pa|qb) etc. from the FP32 copy ovT[x][y][p][q] = (px|qy): o^2 consecutive floats per slice
+  const float* oab = ovT + (1LL * a * v + b) * o2;
+  const float* oac = ovT + (1LL * a * v + c) * o2;
+  const float* obc = ovT + (1LL * b * v + c) * o2;
   for (int idx = threadIdx.x; idx < o2; idx += blockDim.x) {
     const int p = idx / o, q = idx % o;
-    Sab[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + b]);
-    Sac[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + a) * ov + 1LL * q * v + c]);
-    Sbc[p * P1 + q] = static_cast<float>(ovov[(1LL * p * v + b) * ov + 1LL * q * v + c]);
+    Sab[p * P1 + q] = oab[idx];
+    Sac[p * P1 + q] = oac[idx];
+    Sbc[p * P1 + q] = obc[idx];
   }
   for (int y = threadIdx.x; y < o; y += blockDim.x) {
     ta[y] = static_cast<float>(t1[y * v + a]);
@@ -376,29 +379,29 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
   }
   __syncthreads();
   const float* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
-  // W is stored [i][k][j] (j fastest) and read in that order; (y0, y2, y1) of idx advance by the
-  // fixed stride blockDim.x with carries
+  // W is stored [i][k][j] (j fastest). Each thread owns pairs (j, k) = (y1, y2) (consecutive threads:
+  // consecutive j, so every load instruction reads a contiguous row of W) and walks i = y0 with eight
+  // loads in flight; the terms that depend on (j, k) only (t1 of b and c, (bj|ck), d_j + d_k) stay in
+  // registers across the walk.
   constexpr int kLoads = 8;
-  const int st = blockDim.x, d1 = st % o, d2 = (st / o) % o, d0 = st / o2;
-  int y1 = threadIdx.x % o, y2 = (threadIdx.x / o) % o, y0 = threadIdx.x / o2;
-  for (int base = threadIdx.x; base < o3; base += kLoads * st) {
-    float wr[kLoads];
+  for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
+    const int y1 = jk % o, y2 = jk / o;
+    const float tcv = tc[y2], tbv = tb[y1], sbc = Sbc[y1 * P1 + y2], d12 = dm[y1] + dm[y2];
+    const float* wp = Wb + jk;
+    float2* dst = swv + y1 * S1 + y2;
+    for (int i0 = 0; i0 < o; i0 += kLoads) {
+      float wr[kLoads];
 #pragma unroll
-    for (int u = 0; u < kLoads; ++u) wr[u] = base + u * st < o3 ? Wb[base + u * st] : 0.f;
+      for (int u = 0; u < kLoads; ++u) wr[u] = i0 + u < o ? wp[static_cast<long long>(i0 + u) * o2] : 0.f;
 #pragma unroll
-    for (int u = 0; u < kLoads; ++u) {
-      if (base + u * st < o3) {
-        const float disc = Sab[y0 * P1 + y1] * tc[y2] + Sac[y0 * P1 + y2] * tb[y1] + Sbc[y1 * P1 + y2] * ta[y0];
-        const float sc = rsqrtf(dm[y0] + dm[y1] + dm[y2]);
-        swv[y0 * S0 + y1 * S1 + y2] = make_float2(wr[u] * sc, (wr[u] + disc) * sc);
+      for (int u = 0; u < kLoads; ++u) {
+        const int y0 = i0 + u;
+        if (y0 < o) {
+          const float disc = Sab[y0 * P1 + y1] * tcv + Sac[y0 * P1 + y2] * tbv + sbc * ta[y0];
+          const float sc = rsqrtf(dm[y0] + d12);
+          dst[y0 * S0] = make_float2(wr[u] * sc, (wr[u] + disc) * sc);
+        }
       }
-      y1 += d1;
-      int cy = y1 >= o;
-      y1 -= cy ? o : 0;
-      y2 += d2 + cy;
-      cy = y2 >= o;
-      y2 -= cy ? o : 0;
-      y0 += d0 + cy;
     }
   }
   __syncthreads();
@@ -407,13 +410,16 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
   const int x0 = a, x1 = b, x2 = c;
   auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
   auto SS = [&](int p) { return p == 0 ? S0 : (p == 1 ? S1 : 1); };
+  const bool distinct = a < b && b < c;
   bool act[6];
 #pragma unroll
   for (int pi = 0; pi < 6; ++pi) {
     bool dup = false;
+    if (!distinct) {
 #pragma unroll
-    for (int q = 0; q < pi; ++q)
-      dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
+      for (int q = 0; q < pi; ++q)
+        dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
+    }
     act[pi] = !dup;
   }
   constexpr int NL = NLO > 0 ? NLO : 1;
@@ -427,6 +433,63 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
       si[q] = SS(PM[q][0]);
     }
     float acc = 0.f;
+    if (distinct) {
+      // a < b < c: all six orderings are distinct. With w_q, v_q the six placements (q = 0, 3, 4 the
+      // cyclic ones, 1, 2, 5 the others), ordering q has z_q = 3 w_q + S (S the sum of w over q's class)
+      // and y_q = v_q - v_r with r = rev(q) the placement of the reversed slots (0<->5, 3<->1, 4<->2,
+      // always of the other class), so y_r = -y_q. Each pair then contributes
+      // (z_q - z_r) y_q = (3 (w_q - w_r) + S_cyc - S_oth) y_q to the canonical sum, and, since the
+      // i-sums of y_r are minus those of y_q, (sum_i U (z_q - z_r)) (sum_i U y_q) to the projected one:
+      // three products per (i, j, k) instead of six, the same quantities.
+      float2 zp[3][NL];  // (sum_i U (z_q - z_r), sum_i U y_q) per pair and LO
+#pragma unroll
+      for (int h = 0; h < 3; ++h)
+#pragma unroll
+        for (int al = 0; al < NL; ++al) zp[h][al] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int i = 0; i < o; ++i) {
+        float2 p[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          p[q] = swv[off[q]];
+          off[q] += si[q];
+        }
+        const float dS = (p[0].x + p[3].x + p[4].x) - (p[1].x + p[2].x + p[5].x);
+        const float2 d0 = make_float2(fmaf(3.f, p[0].x - p[5].x, dS), p[0].y - p[5].y);
+        const float2 d1 = make_float2(fmaf(3.f, p[3].x - p[1].x, dS), p[3].y - p[1].y);
+        const float2 d2 = make_float2(fmaf(3.f, p[4].x - p[2].x, dS), p[4].y - p[2].y);
+        acc = fmaf(d0.x, d0.y, acc);
+        acc = fmaf(d1.x, d1.y, acc);
+        acc = fmaf(d2.x, d2.y, acc);
+        if constexpr (NLO > 0) {
+          float2 u2[NL];
+          if constexpr (NLO == 1) {
+            u2[0] = reinterpret_cast<const float2*>(U2)[i];
+          } else {
+#pragma unroll
+            for (int h = 0; h < NLO / 2; ++h) {
+              const float4 t = reinterpret_cast<const float4*>(U2)[i * (NLO / 2) + h];
+              u2[2 * h] = make_float2(t.x, t.y);
+              u2[2 * h + 1] = make_float2(t.z, t.w);
+            }
+          }
+#pragma unroll
+          for (int al = 0; al < NLO; ++al) {
+            zp[0][al] = __ffma2_rn(u2[al], d0, zp[0][al]);
+            zp[1][al] = __ffma2_rn(u2[al], d1, zp[1][al]);
+            zp[2][al] = __ffma2_rn(u2[al], d2, zp[2][al]);
+          }
+        }
+      }
+      r_can += static_cast<double>(acc);
+      float f = 0.f;
+#pragma unroll
+      for (int h = 0; h < 3; ++h)
+#pragma unroll
+        for (int al = 0; al < NLO; ++al) f += zp[h][al].x * zp[h][al].y;
+      r_frag += static_cast<double>(f);
+      continue;
+    }
     float2 zy[6][NL];  // (sum_i U z, sum_i U y) per ordering and LO
 #pragma unroll
     for (int pi = 0; pi < 6; ++pi)
@@ -493,6 +556,17 @@ __global__ void __launch_bounds__(256) k_t_energy_f32(const float* __restrict__ 
     }
     out[2 * blk_id] = -s0 / 3.0;
     out[2 * blk_id + 1] = -s1 / 3.0;
+  }
+}
+
+// FP32 copy of (ia|jb) in the order the block energy reads it: ovT[a][b][i][j] = (ia|jb).
+__global__ void k_ovov_t(const double* __restrict__ ovov, float* __restrict__ ovT, int o, int v) {
+  const long long ov = 1LL * o * v, n = ov * ov, oo = 1LL * o * o;
+  for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < n;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(idx % v), j = static_cast<int>((idx / v) % o);
+    const int a = static_cast<int>((idx / ov) % v), i = static_cast<int>(idx / (ov * v));
+    ovT[(1LL * a * v + b) * oo + 1LL * i * o + j] = static_cast<float>(ovov[idx]);
   }
 }
 
@@ -575,9 +649,10 @@ TriplesPlan triples_plan(int o, int v, int N, bool bf, int chunk_mb) {
   p.tpart = static_cast<size_t>(p.nblk) * 2 * 8;
   p.batch = sizeof(BatchEntry) * static_cast<size_t>(std::max(1LL, vv / 2 + v));  // one entry per (b, c >= b)
   p.u = static_cast<size_t>(o) * 8 * 8;  // U padded to at most 8 LOs
+  p.ovt = bf ? static_cast<size_t>(vv * oo) * 4 : 0;  // FP32 (ia|jb) in block-energy order (mixed)
   auto al = [](size_t x) { return (std::max<size_t>(x, 256) + 255) / 256 * 256; };
   p.total = 2 * al(p.xt) + 2 * al(p.to) + al(p.ovoo) + al(p.pbvv) + al(p.ovvv_chunk) + al(p.w) + al(p.tpart) +
-            2 * al(p.batch) + al(p.u);
+            2 * al(p.batch) + al(p.u) + (bf ? al(p.ovt) : 0);
   return p;
 }
 
@@ -761,6 +836,17 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     cudaMemsetAsync(dUp, 0, static_cast<size_t>(o) * nlo_t * 8, s);
     cudaMemcpy2DAsync(dUp, nlo_t * 8, U, nlo * 8, nlo * 8, o, cudaMemcpyDeviceToDevice, s);
   }
+  float* ovT = nullptr;  // k_t_energy_f32 reads (ia|jb) from this FP32 copy
+  if (bf && staged && staged_full) {
+    ovT = static_cast<float*>(tmp_alloc(tp.ovt));
+    if (!ovT) {
+      cleanup();
+      set_error("lnocc_triples: device allocation failed (ovT)");
+      return LNOCC_ENOMEM;
+    }
+    count_launch();
+    k_ovov_t<<<1216, 256, 0, s>>>(ovov, ovT, o, v);
+  }
   auto energy_launch = [&](const void* Wp, long long Sc, int b, int c0, int na, int nc, double* part) {
     dim3 grid(na, nc);
     count_launch();
@@ -769,7 +855,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
   do {                                                                                                   \
     if (staged_full)                                                                                     \
       k_t_energy_f32<K><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps, t1,  \
-                                                 ovov, dUp, part);                                       \
+                                                 ovT, dUp, part);                                        \
     else                                                                                                 \
       k_t_energy_staged<float, float, K, true><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, \
                                                                         c0, o, v, eps, t1, ovov, dUp,    \

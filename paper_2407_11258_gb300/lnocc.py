@@ -50,7 +50,8 @@ class Info(ctypes.Structure):
                 ("model_flops_t", ctypes.c_double), ("exec_flops", ctypes.c_double),
                 ("gemm_launches", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("t_triples_gemm_ms", ctypes.c_double),
-                ("t_triples_ms", ctypes.c_double), ("device_allocs", ctypes.c_longlong)]
+                ("t_triples_ms", ctypes.c_double), ("device_allocs", ctypes.c_longlong),
+                ("floor_spread", ctypes.c_double), ("n_refined", ctypes.c_int), ("diis_restarts", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
