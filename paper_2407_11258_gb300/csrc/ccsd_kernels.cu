@@ -517,12 +517,12 @@ __global__ void k_e2_occ(const double* __restrict__ t2, const double* __restrict
     const long long i = e / vv, ab = e % vv;
     float t[MAXO];
 #pragma unroll
-    for (int k = 0; k < MAXO; ++k) t[k] = k < o ? static_cast<float>(t2[(i * o + k) * vv + ab]) : 0.f;
+    for (int k = 0; k < MAXO; ++k) t[k] = k < o ? f64_to_f32_fields(t2[(i * o + k) * vv + ab]) : 0.f;
     for (int j = 0; j < o; ++j) {
       float acc = 0.f;
 #pragma unroll
       for (int k = 0; k < MAXO; ++k) acc = fmaf(t[k], Fs[k][j], acc);
-      S[(i * o + j) * vv + ab] -= static_cast<double>(acc);
+      S[(i * o + j) * vv + ab] -= f32_to_f64_fields(acc);
     }
   }
 }
@@ -532,8 +532,10 @@ __global__ void k_e2_occ(const double* __restrict__ t2, const double* __restrict
 //   B^_vv[Q][a][c] = B_vv[Q][a][c] - sum_k t_k^a B_ov[Q][k][c]
 //   B^_vo[Q][a][i] += sum_c B_vv[Q][a][c] t_i^c
 // Both corrections are length-o / length-v dot products on data read once, so the pass is bound by the
-// traffic of B_vv (read) and B^_vv (written); products and sums in FP32 (relative error ~1e-7),
-// the dressed factors stay FP64. One warp per row; the v-sums end in a fixed-order warp butterfly.
+// traffic of B_vv (read) and B^_vv (written); products, sums and the difference in FP32 (relative
+// error ~1e-7; every consumer of B^_vv on the mixed path splits it into BF16 hi/lo, 16 bits), the
+// conversions through the IEEE fields (no FP64-pipe work per element), the dressed factors stored as
+// FP64. One warp per row; the v-sums end in a fixed-order warp butterfly.
 template <int MAXO>
 __global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restrict__ Bov,
                            const double* __restrict__ t1, double* __restrict__ Bvv_h, double* __restrict__ Bvo_h,
@@ -566,7 +568,7 @@ __global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restr
       for (int t = 0; t < 8; ++t) {
         const int c = c0 + 32 * t;
         if (c >= v) break;
-        const float xf = static_cast<float>(xs[t]);
+        const float xf = f64_to_f32_fields(xs[t]);
         float corr = 0.f;
 #pragma unroll
         for (int k = 0; k < MAXO; ++k)
@@ -574,7 +576,7 @@ __global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restr
             corr = fmaf(ta[k], bs[k * v + c], corr);
             acc[k] = fmaf(xf, ts[k * v + c], acc[k]);
           }
-        orow[c] = xs[t] - static_cast<double>(corr);
+        orow[c] = f32_to_f64_fields(xf - corr);
       }
     }
 #pragma unroll

@@ -56,12 +56,13 @@ __device__ __forceinline__ long long view_off(const View& v, long long r, int k)
   return view_roff(v, static_cast<int>(r)) + view_koff(v, k);
 }
 
-// Store scale * x: BF16 hi/lo planes (scale applied in FP32: the values keep ~16 bits anyway) or FP64.
+// Store scale * x: BF16 hi/lo planes (x truncated to FP32 through its fields and the scale applied in
+// FP32: the values keep ~16 bits anyway) or FP64.
 template <bool BF16>
 __device__ __forceinline__ void put(void* out, long long idx, long long plane, double x, double scale) {
   if (BF16) {
     __nv_bfloat16 hi, lo;
-    const float xf = static_cast<float>(x) * static_cast<float>(scale);
+    const float xf = f64_to_f32_fields(x) * static_cast<float>(scale);
     hi = __float2bfloat16_rn(xf);
     lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
     __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);

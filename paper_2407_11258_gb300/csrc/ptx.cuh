@@ -200,13 +200,50 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// FP64 <-> FP32 through the IEEE-754 fields with integer operations only (GB300's FP64 pipe, which the
+// conversion instructions occupy, runs at a small fraction of the FP32 rate). f64_to_f32_fields
+// truncates the mantissa to 23 bits (relative error below 2^-23), flushes values under the FP32 normal
+// range to signed zero and sends values above it to infinity; NaN stays NaN, infinity stays infinity.
+// f32_to_f64_fields is exact for normal FP32 values (FP32 subnormals become zero).
+__device__ __forceinline__ float f64_to_f32_fields(double x) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = static_cast<unsigned>(u >> 32), lo = static_cast<unsigned>(u);
+  const unsigned sign = hi & 0x80000000u, frac_hi = hi & 0xfffffu;
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+  const unsigned m = (frac_hi << 3) | (lo >> 29);  // the 23 leading fraction bits
+  unsigned r;
+  if (e == 0x7ff)
+    r = sign | 0x7f800000u | m | ((frac_hi | lo) != 0u ? 0x400000u : 0u);
+  else if (e <= 896)
+    r = sign;
+  else if (e >= 896 + 255)
+    r = sign | 0x7f800000u;
+  else
+    r = sign | (static_cast<unsigned>(e - 896) << 23) | m;
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double f32_to_f64_fields(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, fe = (u >> 23) & 0xffu, fm = u & 0x7fffffu;
+  unsigned hi, lo = 0u;
+  if (fe == 0u) {
+    hi = sign;
+  } else if (fe == 0xffu) {
+    hi = sign | 0x7ff00000u | (fm >> 3) | (fm != 0u ? 0x80000u : 0u);
+  } else {
+    hi = sign | ((fe + 896u) << 20) | (fm >> 3);
+    lo = fm << 29;
+  }
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | lo));
+}
+
 // BF16 split of an FP64 value: hi = bf16(x), lo = bf16(x - hi). hi*b_hi + hi*b_lo + lo*b_hi keeps
 // about 16 significant bits of every product (the lo*lo term, ~2^-16 relative, is dropped).
-// The residual is formed in FP32 from x rounded to FP32 (exact subtraction; the 2^-24 rounding of x
-// is far below the ~2^-16 the pair keeps): one FP64 conversion per element, no FP64 arithmetic, which
+// The residual is formed in FP32 from x truncated to FP32 through its fields (exact subtraction; the
+// 2^-23 truncation of x is far below the ~2^-16 the pair keeps): no FP64-pipe work per element, which
 // matters on a part whose FP64 pipe is a small fraction of its FP32 rate.
 __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  const float xf = static_cast<float>(x);
+  const float xf = f64_to_f32_fields(x);
   hi = __float2bfloat16_rn(xf);
   lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
 }

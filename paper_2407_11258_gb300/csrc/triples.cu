@@ -330,12 +330,14 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
 //  * w and v of one (y0, y1, y2) sit side by side, so a placement is one 8-byte shared-memory load;
 //  * the projected i-sums of z and y for one LO form a pair updated by one packed FP32 FMA, with
 //    U[i][alpha] duplicated into both halves of a pair in shared memory.
-template <int NLO>
-__global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2) k_t_energy_f32(const float* __restrict__ W, long long slot_stride, int b, int c0,
-                                                      int o, int v, const double* __restrict__ eps,
-                                                      const double* __restrict__ t1, const float* __restrict__ ovT,
-                                                      const double* __restrict__ U, double* __restrict__ out) {
+// OC > 0: compiled for nocc = OC (constant strides and trip counts); OC = 0: any nocc (o_in).
+template <int NLO, int OC>
+__global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
+    k_t_energy_f32(const float* __restrict__ W, long long slot_stride, int b, int c0, int o_in, int v,
+                   const double* __restrict__ eps, const double* __restrict__ t1, const float* __restrict__ ovT,
+                   const double* __restrict__ U, double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  const int o = OC > 0 ? OC : o_in;
   const int slot = blockIdx.y, a = blockIdx.x;
   const int c = c0 + slot;
   const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
@@ -854,8 +856,12 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
 #define LN_F(K)                                                                                          \
   do {                                                                                                   \
     if (staged_full)                                                                                     \
-      k_t_energy_f32<K><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps, t1,  \
-                                                 ovT, dUp, part);                                        \
+      if (o == 16)                                                                                       \
+        k_t_energy_f32<K, 16><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps, \
+                                                       t1, ovT, dUp, part);                              \
+      else                                                                                               \
+        k_t_energy_f32<K, 0><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps,  \
+                                                      t1, ovT, dUp, part);                               \
     else                                                                                                 \
       k_t_energy_staged<float, float, K, true><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, \
                                                                         c0, o, v, eps, t1, ovov, dUp,    \
@@ -901,11 +907,16 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       auto attr = [](const void* fn) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       };
-      attr(reinterpret_cast<const void*>(k_t_energy_f32<0>));
-      attr(reinterpret_cast<const void*>(k_t_energy_f32<1>));
-      attr(reinterpret_cast<const void*>(k_t_energy_f32<2>));
-      attr(reinterpret_cast<const void*>(k_t_energy_f32<4>));
-      attr(reinterpret_cast<const void*>(k_t_energy_f32<8>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<0, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<0, 16>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<1, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<1, 16>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<2, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<2, 16>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<4, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<4, 16>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<8, 0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_f32<8, 16>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, false>));
