@@ -456,22 +456,27 @@ def mlp_measure(lnocc, synth, ntrain, nheld, nheld_fp64, train_steps, batch, pre
         losses.append(m.train_step(X[sel].contiguous(), dt[sel].contiguous(), lr))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    it0, it1, t_mp2, t_mlp, de, fallbacks = [], [], [], [], [], 0
+    it0, it1, t_mp2, t_mlp, de, fallbacks, noconv = [], [], [], [], [], 0, []
     for k in range(2000, 2000 + nheld):
         o, v, q, eps, B, U = synth.mlp_fragment_device(k, dev)
         f = lnocc.lnocc_build_ints(o, v, q, eps, B, lnocc.default_opts(precision=prec))
         lnocc.lnocc_frag_set_mlp(f, m)
         torch.cuda.synchronize()
         a = time.perf_counter()
-        e0, n0, _ = lnocc.lnocc_ccsd(f, allow_noconv=True)
+        e0, n0, s0 = lnocc.lnocc_ccsd(f, allow_noconv=True)
         b = time.perf_counter()
-        e1, n1, _ = lnocc.lnocc_ccsd(f, guess_mode=lnocc.LNOCC_GUESS_MLP, allow_noconv=True)
+        e1, n1, s1 = lnocc.lnocc_ccsd(f, guess_mode=lnocc.LNOCC_GUESS_MLP, allow_noconv=True)
         c = time.perf_counter()
         it0.append(n0)
         it1.append(n1)
         t_mp2.append(b - a)
         t_mlp.append(c - b)
-        de.append(abs(e1 - e0))
+        # energies compare where both solves converged; a solve stopped at the mixed noise floor
+        # (ENOCONV, energy spread above 1e-7 Eh) is counted apart
+        if s0 == lnocc.LNOCC_OK and s1 == lnocc.LNOCC_OK:
+            de.append(abs(e1 - e0))
+        else:
+            noconv.append((k, int(s0), int(s1), abs(e1 - e0)))
         f.free()
     # the same comparison on the FP64 path, where converged energies can be compared at 1e-8 Eh
     it0_64, it1_64, de_64 = [], [], []
@@ -494,7 +499,12 @@ def mlp_measure(lnocc, synth, ntrain, nheld, nheld_fp64, train_steps, batch, pre
         "mean_iterations_mp2_guess": float(np.mean(it0)), "mean_iterations_mlp_guess": float(np.mean(it1)),
         "mean_ccsd_s_mp2_guess": float(np.mean(t_mp2)), "mean_ccsd_s_mlp_guess": float(np.mean(t_mlp)),
         "held_out_solves_per_s_mlp_guess": nheld / sum(t_mlp),
-        "max_abs_dE_mlp_vs_mp2_guess": float(np.max(de)),
+        "max_abs_dE_mlp_vs_mp2_guess": float(np.max(de)) if de else None,
+        "n_both_converged": len(de),
+        "noise_floor_stops": {"count": len(noconv),
+                              "max_abs_dE": float(max(x[3] for x in noconv)) if noconv else None,
+                              "note": "fragments where either solve stopped at the mixed noise floor (ENOCONV: "
+                                      "energy spread > 1e-7 Eh; opts.n_refine would refine them in FP64)"},
         "fp64_path": {"n_frag": nheld_fp64,
                       "mean_iterations_mp2_guess": float(np.mean(it0_64)) if it0_64 else None,
                       "mean_iterations_mlp_guess": float(np.mean(it1_64)) if it1_64 else None,

@@ -56,6 +56,13 @@ extern "C" {
  * in L2 between its store and its two reductions), the second sigma4 and sigma6. GROUPED needs
  * nocc = 16 (one 256-column accumulator holds the (y, z) plane; 128 rows hold whole a values); AUTO
  * takes it there and PER_TERM elsewhere, and GROUPED falls back to PER_TERM for other nocc. */
+/* Device memory of a handle (and of its lnocc_triples temporaries). CACHED: stream-ordered allocations
+ * from one library-wide pool per device that keeps freed memory for later handles (no cudaMalloc /
+ * cudaFree, and no device synchronisation, once the pool holds enough; lnocc_trim_pool returns the
+ * unused part to the device). DIRECT: cudaMalloc / cudaFree per buffer. */
+#define LNOCC_MEM_CACHED 0
+#define LNOCC_MEM_DIRECT 1
+
 #define LNOCC_TK_AUTO 0
 #define LNOCC_TK_PER_TERM 1
 #define LNOCC_TK_GROUPED 2
@@ -85,7 +92,8 @@ typedef struct lnocc_opts {
                            workspace size that lnocc_workspace_bytes reports */
   int triples_kernel;   /* (T) contraction launches on the mixed path: LNOCC_TK_AUTO (0, the default),
                            LNOCC_TK_PER_TERM or LNOCC_TK_GROUPED (same W, same energy) */
-  int reserved[3];
+  int memory;           /* LNOCC_MEM_CACHED (0, the default) or LNOCC_MEM_DIRECT, see below */
+  int reserved[2];
 } lnocc_opts;
 
 typedef struct lnocc_info {
@@ -461,8 +469,13 @@ int lnocc_frag_set_mlp(lnocc_frag* f, const lnocc_mlp* m);
 /* Copy the handle's bookkeeping (energies, iteration count, flop counters) into *info. */
 int lnocc_frag_info(const lnocc_frag* f, lnocc_info* info);
 
-/* Release everything the handle holds (safe on NULL). */
+/* Release everything the handle holds (safe on NULL). With LNOCC_MEM_CACHED its device memory goes back
+ * to the library's pool (stream-ordered on the handle's stream), not to the device. */
 int lnocc_free_fragment(lnocc_frag* f);
+
+/* Return the unused memory of the library's cached pool on the current device to the device (after
+ * synchronising the device). Handles still alive keep theirs. Returns LNOCC_OK or LNOCC_ECUDA. */
+int lnocc_trim_pool(void);
 
 /* Message of the last failing call on this thread ("" when none). */
 const char* lnocc_last_error(void);

@@ -3,6 +3,8 @@
 
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -15,6 +17,35 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace lnocc
 
 using lnocc::Frag;
+
+namespace lnocc {
+cudaMemPool_t cached_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t p = nullptr;
+  if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  unsigned long long keep = ~0ULL;  // keep freed memory for later handles
+  cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = p;
+  return p;
+}
+}  // namespace lnocc
 
 extern "C" {
 
@@ -49,7 +80,8 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
   if (opts) o = *opts;
   if ((o.precision != LNOCC_PREC_FP64 && o.precision != LNOCC_PREC_MIXED) || o.max_iter < 0 || o.diis_space < 0 ||
       o.diis_space > 8 || o.n_refine < 0 || (o.graph != 0 && o.graph != 1) || !(o.conv_rms > 0) || !(o.conv_energy > 0) ||
-      o.triples_chunk_mb < 0 || o.triples_kernel < LNOCC_TK_AUTO || o.triples_kernel > LNOCC_TK_GROUPED) {
+      o.triples_chunk_mb < 0 || o.triples_kernel < LNOCC_TK_AUTO || o.triples_kernel > LNOCC_TK_GROUPED ||
+      (o.memory != LNOCC_MEM_CACHED && o.memory != LNOCC_MEM_DIRECT)) {
     lnocc::set_error("lnocc_build_ints: bad options");
     return LNOCC_EINVAL;
   }
@@ -63,6 +95,10 @@ int lnocc_build_ints(int nocc, int nvir, int naux, const double* eps, const doub
   f.opts = o;
   f.mixed = (o.precision == LNOCC_PREC_MIXED);
   f.s = static_cast<cudaStream_t>(stream);
+  if (o.memory == LNOCC_MEM_CACHED) {
+    f.pool = lnocc::cached_pool();
+    f.pool_cached = f.pool != nullptr;
+  }
   const char* pe = std::getenv("LNOCC_PROFILE");
   f.prof = pe && pe[0] == '1';
   lnocc::gemm_stats() = lnocc::GemmStats{};
@@ -270,6 +306,16 @@ int lnocc_autotune_stats(long long* entries, long long* hits, long long* misses,
 int lnocc_free_fragment(lnocc_frag* h) {
   if (h && lnocc::split_ws().p == h->f.splitk) lnocc::split_ws() = lnocc::SplitWs{};
   delete h;
+  return LNOCC_OK;
+}
+
+int lnocc_trim_pool(void) {
+  cudaMemPool_t p = lnocc::cached_pool();
+  if (!p) return LNOCC_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(p, 0) != cudaSuccess) {
+    lnocc::set_error(std::string("lnocc_trim_pool: ") + cudaGetErrorString(cudaGetLastError()));
+    return LNOCC_ECUDA;
+  }
   return LNOCC_OK;
 }
 

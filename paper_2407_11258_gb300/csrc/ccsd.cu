@@ -97,6 +97,15 @@ Frag::~Frag() {
   for (auto& m : marks) cudaEventDestroy(m.second);
   if (gexec) cudaGraphExecDestroy(gexec);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (pool_cached && !allocs.empty()) {
+    // the caller's stream of the last call orders the frees; if it is gone, wait for the device and
+    // free on the legacy stream
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaDeviceSynchronize();
+      s = nullptr;
+    }
+  }
   for (void* p : allocs) dev_free(p);
   if (h_scal && h_scal != h_ext) cudaFreeHost(h_scal);
 }

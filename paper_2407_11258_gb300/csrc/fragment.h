@@ -53,6 +53,7 @@ struct Frag {
   bool oom = false;
   bool scratch_overflow = false;
   cudaMemPool_t pool = nullptr;
+  bool pool_cached = false;  // `pool` is the library-wide cached pool (the caller's stream, not a batch's)
   double* h_ext = nullptr;  // caller-owned pinned host buffer (16 doubles) used instead of cudaMallocHost
   void* ws_ext = nullptr;  // caller-owned workspace for the (T) temporaries (lnocc_frag_set_workspace)
   size_t ws_ext_bytes = 0;

@@ -152,6 +152,9 @@ int autotune_mode(int mode);
 // mode 1). Timing allocates a scratch output and synchronizes, which callers that must not allocate
 // or synchronize cannot allow.
 bool& autotune_timing_allowed();
+// The library-wide stream-ordered pool of the current device (created on first use, keeps freed memory;
+// nullptr if the device cannot create one).
+cudaMemPool_t cached_pool();
 void autotune_stats(long long out[4]);  // entries, hits, misses, shapes tuned
 bool autotune_save(const char* path);
 bool autotune_load(const char* path);

@@ -17,6 +17,7 @@ LNOCC_PREC_FP64, LNOCC_PREC_MIXED = 0, 1
 LNOCC_GUESS_MP2, LNOCC_GUESS_GIVEN, LNOCC_GUESS_MLP = 0, 1, 2
 LNOCC_FAULT_NAN_INPUT, LNOCC_FAULT_ZERO_DIIS = 1, 2
 LNOCC_TK_AUTO, LNOCC_TK_PER_TERM, LNOCC_TK_GROUPED = 0, 1, 2
+LNOCC_MEM_CACHED, LNOCC_MEM_DIRECT = 0, 1
 
 ERR_NAMES = {0: "LNOCC_OK", 1: "LNOCC_EINVAL", 2: "LNOCC_ENOMEM", 3: "LNOCC_ENOCONV", 4: "LNOCC_ENUMERIC",
              5: "LNOCC_ETIMEOUT", 6: "LNOCC_ECUDA"}
@@ -33,14 +34,15 @@ EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragme
            "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp", "lnocc_mp2_workspace_bytes",
            "lnocc_mp2_energy", "lnocc_workspace_bytes", "lnocc_frag_set_workspace", "lnocc_debug_wait",
            "lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space",
-           "lnocc_kpoint_df"]
+           "lnocc_kpoint_df", "lnocc_trim_pool"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("diis_space", ctypes.c_int),
                 ("n_refine", ctypes.c_int), ("conv_rms", ctypes.c_double), ("conv_energy", ctypes.c_double),
                 ("fault_inject", ctypes.c_int), ("verbose", ctypes.c_int), ("graph", ctypes.c_int),
-                ("triples_chunk_mb", ctypes.c_int), ("triples_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("triples_chunk_mb", ctypes.c_int), ("triples_kernel", ctypes.c_int), ("memory", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Info(ctypes.Structure):
@@ -101,6 +103,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lnocc_gemm_noalloc.argtypes = [I, I, I, I, P, P, P, P]
     lib.lnocc_frag_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lnocc_free_fragment.argtypes = [P]
+    lib.lnocc_trim_pool.argtypes = []
     lib.lnocc_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
     lib.lnocc_default_batch_opts.restype = None
     lib.lnocc_solve_batch.argtypes = [I, ctypes.POINTER(BatchItem), ctypes.POINTER(Opts), ctypes.POINTER(BatchOpts),
@@ -208,6 +211,11 @@ def _check(code, ok=(LNOCC_OK,)):
     if code not in ok:
         raise LnoccError(code, load().lnocc_last_error().decode())
     return code
+
+
+def lnocc_trim_pool():
+    """Return the unused memory of the library's cached device pool to the device."""
+    _check(load().lnocc_trim_pool())
 
 
 def default_opts(**kw) -> Opts:
