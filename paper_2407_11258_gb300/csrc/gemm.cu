@@ -475,10 +475,14 @@ struct TcCfg {
   // (BN = 256, the grouped (T) launches: two 4 KB W boxes per warp)
   static constexpr int EPI_BYTES0 = 4 * 32 * 17 * 4 > 4 * (BN * 8 + BN / 4) ? 4 * 32 * 17 * 4 : 4 * (BN * 8 + BN / 4);
   static constexpr int EPI_BYTES = BN == 256 && EPI_BYTES0 < 32768 ? 32768 : EPI_BYTES0;
-  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 4 ? 4 : (192 * 1024) / STAGE_BYTES;
+  // as many stages (up to 4) as fit in the 227 KB of shared memory a CTA may hold beside the epilogue
+  // scratch, the 1 KB alignment slack and the barriers
+  static constexpr int STAGE_ROOM = 232448 - EPI_BYTES - 1024 - 256;
+  static constexpr int STAGES = STAGE_ROOM / STAGE_BYTES > 4 ? 4 : STAGE_ROOM / STAGE_BYTES;
   static constexpr int ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two accumulators: MMA of tile t+1 overlaps epilogue of t
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(STAGES >= 2 && SMEM <= 232448, "pipeline does not fit the shared memory of one CTA");
 };
 
 // Arguments of one tcgen05 GEMM launch. Two K segments: C = A0 B0^T (nkb0 blocks) + A1 B1^T (nkb1 blocks)

@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
       for (int h = 0; h < 3; ++h)
 #pragma unroll
         for (int al = 0; al < NL; ++al) zp[h][al] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll (OC > 0 ? OC : 2)
       for (int i = 0; i < o; ++i) {
         float2 p[6];
 #pragma unroll
@@ -573,6 +573,38 @@ __global__ void k_ovov_t(const double* __restrict__ ovov, float* __restrict__ ov
 }
 
 // Sum of the per-block partials in a fixed order: out[0] canonical, out[1] projected.
+// Block g sums partials [g * chunk, min((g + 1) * chunk, nblk)) into out[2g], out[2g + 1] (the first of
+// two fixed-order passes; one 1024-thread block alone took about 1.3 ms for the 2.3e6 block partials
+// of a diamond-like call).
+__global__ void k_t_finish_part(const double* part, long long nblk, long long chunk, double* out) {
+  __shared__ double sh[2][32];
+  double s0 = 0.0, s1 = 0.0;
+  const long long i0 = blockIdx.x * chunk, i1 = min(nblk, i0 + chunk);
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    s0 += part[2 * i];
+    s1 += part[2 * i + 1];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) {
+    sh[0][w] = s0;
+    sh[1][w] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
+      a0 += sh[0][q];
+      a1 += sh[1][q];
+    }
+    out[2 * blockIdx.x] = a0;
+    out[2 * blockIdx.x + 1] = a1;
+  }
+}
+
 __global__ void k_t_finish(const double* part, long long nblk, double* out) {
   __shared__ double sh[2][32];
   double s0 = 0.0, s1 = 0.0;
@@ -648,7 +680,7 @@ TriplesPlan triples_plan(int o, int v, int N, bool bf, int chunk_mb) {
   p.w = static_cast<size_t>(p.welems) * esz;
   p.nblk = 0;
   for (int b = 0; b < v; ++b) p.nblk += 1LL * (b + 1) * (v - b);
-  p.tpart = static_cast<size_t>(p.nblk) * 2 * 8;
+  p.tpart = static_cast<size_t>(p.nblk + 256) * 2 * 8;  // block partials, then 256 first-pass sums
   p.batch = sizeof(BatchEntry) * static_cast<size_t>(std::max(1LL, vv / 2 + v));  // one entry per (b, c >= b)
   p.u = static_cast<size_t>(o) * 8 * 8;  // U padded to at most 8 LOs
   p.ovt = bf ? static_cast<size_t>(vv * oo) * 4 : 0;  // FP32 (ia|jb) in block-energy order (mixed)
@@ -1048,7 +1080,13 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
                                                         ovov, dU, nlo, tpart + 2 * ch.part);
     }
   }
-  k_t_finish<<<1, 1024, 0, s>>>(tpart, nblk_total, scal + 4);
+  {
+    constexpr int kParts = 256;  // first-pass blocks; their sums sit after the nblk block partials
+    const long long chunk = (nblk_total + kParts - 1) / kParts;
+    count_launch(2);
+    k_t_finish_part<<<kParts, 1024, 0, s>>>(tpart, nblk_total, chunk, tpart + 2 * nblk_total);
+    k_t_finish<<<1, 1024, 0, s>>>(tpart + 2 * nblk_total, kParts, scal + 4);
+  }
   cudaMemcpyAsync(h_scal + 4, scal + 4, 16, cudaMemcpyDeviceToHost, s);
   cudaEventRecord(ev_call1, s);
   cudaStreamSynchronize(s);
