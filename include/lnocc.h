@@ -54,8 +54,9 @@ extern "C" {
  * sigma4, sigma6, sigma5) per chunk. GROUPED: two launches per chunk; the first runs sigma1 + sigma2,
  * sigma3 and sigma5 of one (c, 128-row tile of (a, x)) block back to back in one CTA (the block stays
  * in L2 between its store and its two reductions), the second sigma4 and sigma6. GROUPED needs
- * nocc = 16 (one 256-column accumulator holds the (y, z) plane; 128 rows hold whole a values); AUTO
- * takes it there and PER_TERM elsewhere, and GROUPED falls back to PER_TERM for other nocc. */
+ * nocc = 16 or 32 (128 rows hold whole a values; the (y, z) plane is one or four 256-column
+ * accumulator tiles); AUTO takes it there and PER_TERM elsewhere, and GROUPED falls back to PER_TERM
+ * for other nocc. */
 /* Device memory of a handle (and of its lnocc_triples temporaries). CACHED: stream-ordered allocations
  * from one library-wide pool per device that keeps freed memory for later handles (no cudaMalloc /
  * cudaFree, and no device synchronisation, once the pool holds enough; lnocc_trim_pool returns the

@@ -510,7 +510,7 @@ struct TileInfo {
   long long cbase;
   int nkb1, N;                 // second-segment K blocks and valid columns of this tile
   int ma0, mb0, ma1, mb1;      // tensor maps (0..3 = tA0, tB0, tA1, tB1) of the two segments
-  int omap, cz;                // grouped launches: term (output map) and the region's W chunk c coordinate
+  int omap, cz, ct;            // grouped launches: term (output map), region's W chunk c, column tile
 };
 
 // Grouped (T) launch: regions of one W chunk, each computed by one CTA as 3 (kind 1) or 2 (kind 2)
@@ -524,12 +524,16 @@ struct TileInfo {
 // values (kind 1) or 2 whole i values of one a (kind 2)), so the ordering of a region's store before
 // its reductions is the warp's own (a wait on its bulk groups), with no barrier across warps.
 __device__ __forceinline__ bool grp_tile(const GrpSpec& g, int w, TileInfo& ti) {
-  const int terms = g.kind == 1 ? 3 : 2;
-  const int r = blockIdx.x + (w / terms) * gridDim.x;
+  // kind 1: 3 terms x ncol column tiles of 256 per region (all tiles of a term before the next term)
+  const int per = g.kind == 1 ? 3 * g.ncol : 2;
+  const int r = blockIdx.x + (w / per) * gridDim.x;
   if (r >= g.nreg) return false;
-  const int term = w % terms;
+  const int q = w % per;
+  const int term = g.kind == 1 ? q / g.ncol : q;
+  const int ct = g.kind == 1 ? q % g.ncol : 0;
   ti.valid = true;
-  ti.n0 = 0;
+  ti.n0 = ct * 256;
+  ti.ct = ct;
   ti.z = 0;
   ti.kb0 = 0;
   ti.nkbA = g.nkb;
@@ -545,14 +549,16 @@ __device__ __forceinline__ bool grp_tile(const GrpSpec& g, int w, TileInfo& ti) 
     ti.N = g.oo;
     ti.cbase = cl * g.Sc;
     ti.cz = cl;
+    // B rows: the (y, z) plane of c (TO) or b (TOT); the producer adds n0 = 256 ct for the column tile
+    const int bc = c * g.oo, bb = g.b * g.oo;
     if (term == 0) {
-      ti.ma0 = 0; ti.a_row0 = g.bvo;          ti.mb0 = 1; ti.b_row0 = c * g.oo;
-      ti.ma1 = 0; ti.a_row1 = c * g.vo;       ti.mb1 = 3; ti.b_row1 = g.b * g.oo;
+      ti.ma0 = 0; ti.a_row0 = g.bvo;          ti.mb0 = 1; ti.b_row0 = bc;
+      ti.ma1 = 0; ti.a_row1 = c * g.vo;       ti.mb1 = 3; ti.b_row1 = bb;
       ti.nkb1 = g.nkb;
     } else if (term == 1) {
-      ti.ma0 = 2; ti.a_row0 = g.bvo;          ti.mb0 = 1; ti.b_row0 = c * g.oo;
+      ti.ma0 = 2; ti.a_row0 = g.bvo;          ti.mb0 = 1; ti.b_row0 = bc;
     } else {
-      ti.ma0 = 2; ti.a_row0 = c * g.vo;       ti.mb0 = 3; ti.b_row0 = g.b * g.oo;
+      ti.ma0 = 2; ti.a_row0 = c * g.vo;       ti.mb0 = 3; ti.b_row0 = bb;
     }
   } else {
     const int cb = r / g.mt, cs = g.c0 + cb * g.cblk;
@@ -601,6 +607,7 @@ __device__ __forceinline__ TileInfo tile_info(const TcArgs& p, int t) {
   ti.mb1 = 3;
   ti.omap = 0;
   ti.cz = 0;
+  ti.ct = 0;
   ti.valid = ti.m0 < ti.M && ti.nkbA + p.nkb1 > 0;
   return ti;
 }
@@ -706,6 +713,73 @@ __device__ __forceinline__ void grp_epilogue(const TcArgs& p, const TileInfo& ti
         }
       } else {
         tma_reduce_add_5d(tW0, buf, 0, 0, i0, a0, ti.cz + 2 * cc);
+      }
+      bulk_commit();
+    }
+    ++nbox;
+  }
+}
+
+// The same at nocc = 32: W viewed as {j, k, i, a, c} with 32 per occupied axis, every box 32 x 32 FP32
+// with 128-byte rows under the 128-byte swizzle (byte x holds logical byte x ^ (((x >> 7) & 7) << 4)).
+// A warp's 32 rows are one whole a (kind 1) or one whole i of one a (kind 2); chunk cc of column tile
+// ct is one value of the column's outer index:
+//   kind 1, term 0 (sigma1 + sigma2): rows (a, i), cols (k, j), k = 8 ct + cc; box [i][j] at (0, k, 0, a0, c)
+//   kind 1, term 1 (sigma3):          rows (a, j), cols (k, i), same k;          box [i][j], same place
+//   kind 1, term 2 (sigma5):          rows (a, k), cols (i, j), i = 8 ct + cc;  box [k][j] at (0, 0, i, a0, c)
+//   kind 2, term 0 (sigma4):          rows (a, i, k), cols (c, j), c = cz + cc; box [k][j] at (0, 0, i0, a0, c)
+//   kind 2, term 1 (sigma6):          rows (a, i, j), cols (c, k), same c;       box [k][j], same place
+// A "row" term (thread = box row) stores 8 16-byte chunks per thread, a "column" term (thread = box
+// column: sigma3, sigma6) 32 scalars; the swizzle keeps both free of bank conflicts.
+template <int BN>
+__device__ __forceinline__ void grp_epilogue32(const TcArgs& p, const TileInfo& ti, const CUtensorMap* tW0,
+                                               const CUtensorMap* tW1, uint32_t acc, uint32_t sbox, int ew,
+                                               int lane, int& nbox) {
+  constexpr int O = 32;
+  const GrpSpec& g = p.g;
+  const int term = ti.omap;
+  const int mb = ti.m0 + ew * 32;
+  const int a0 = g.kind == 1 ? mb / O : mb / (O * O);
+  const int i0 = g.kind == 1 ? 0 : (mb / O) % O;
+  if (a0 > g.b) return;
+  const bool col_term = term == 1;  // sigma3 (kind 1) and sigma6 (kind 2)
+  const uint32_t x = static_cast<uint32_t>(lane & 7);
+#pragma unroll 1
+  for (int cc = 0; cc < BN / 32; ++cc) {
+    if (g.kind == 2 && ti.cz + cc >= g.nc) break;  // c past the chunk
+    float v[32];
+    tmem_ld32(acc + cc * 32, v);
+    const uint32_t buf = sbox + (nbox & 1) * 4096;
+    if (lane == 0) bulk_wait_read1();
+    __syncwarp();
+    if (!col_term) {
+      const uint32_t base = buf + lane * 128;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        st_shared_v4(base + ((static_cast<uint32_t>(q) ^ x) << 4), v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+      // column `lane` of the box: row r holds the accumulator column r
+      const uint32_t jc = static_cast<uint32_t>(lane >> 2), jw = static_cast<uint32_t>(lane & 3) * 4;
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        st_shared_f32(buf + r * 128 + ((jc ^ static_cast<uint32_t>(r & 7)) << 4) + jw, v[r]);
+    }
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+      if (g.kind == 1) {
+        const int kk = 8 * ti.ct + cc;
+        if (term == 0) {
+          tma_store_5d(tW0, buf, 0, kk, 0, a0, ti.cz);
+        } else {
+          if (term == 1 && ti.ct == 0 && cc == 0) bulk_wait_all();  // the region's stores are performed first
+          if (term == 1)
+            tma_reduce_add_5d(tW0, buf, 0, kk, 0, a0, ti.cz);
+          else
+            tma_reduce_add_5d(tW1, buf, 0, 0, kk, a0, ti.cz);
+        }
+      } else {
+        tma_reduce_add_5d(tW0, buf, 0, 0, i0, a0, ti.cz + cc);
       }
       bulk_commit();
     }
@@ -858,7 +932,10 @@ __global__ void __launch_bounds__(256, 1)
       const OutMap& C = grp ? p.Cg[ti.omap] : p.C;
       if (grp) {
         // W boxes: 2 x 4 KB per epilogue warp in the epilogue scratch (1024-byte aligned)
-        grp_epilogue<BN>(p, ti, &tW0, &tW1, acc, smem_u32(epi) + ew * 8192, ew, lane, nbox);
+        if (p.g.o == 32)
+          grp_epilogue32<BN>(p, ti, &tW0, &tW1, acc, smem_u32(epi) + ew * 8192, ew, lane, nbox);
+        else
+          grp_epilogue<BN>(p, ti, &tW0, &tW1, acc, smem_u32(epi) + ew * 8192, ew, lane, nbox);
       } else if (f32_direct) {
         // FP32 destination, beta 0 or 1 (the (T) W terms). Each epilogue warp computes the column
         // offsets of the tile once into its own shared-memory slot, with a flag per group of 4 columns
@@ -1312,23 +1389,26 @@ static TcArgs tc_args(int M, int N, int nkb0, int nkb1, const OutMap& C, int* ds
   return a;
 }
 
-// The FP32 W chunk [c][a][i][k][j] (nocc = 16) as the 5-D tensor {j, k, i, a, c}; 64-byte swizzled boxes.
+// The FP32 W chunk [c][a][i][k][j] as the 5-D tensor {j, k, i, a, c}; boxes 64-byte swizzled at nocc 16
+// (rows of 16 floats), 128-byte swizzled at nocc 32 (rows of 32 floats).
 static bool make_wmap(CUtensorMap* map, float* W, const GrpSpec& g, const cuuint32_t box[5]) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[5] = {16, 16, 16, static_cast<cuuint64_t>(g.b + 1), static_cast<cuuint64_t>(g.nc)};
-  cuuint64_t strides[4] = {16 * 4, 256 * 4, 4096 * 4, static_cast<cuuint64_t>(g.Sc) * 4};
+  const cuuint64_t o = static_cast<cuuint64_t>(g.o);
+  cuuint64_t dims[5] = {o, o, o, static_cast<cuuint64_t>(g.b + 1), static_cast<cuuint64_t>(g.nc)};
+  cuuint64_t strides[4] = {o * 4, o * o * 4, o * o * o * 4, static_cast<cuuint64_t>(g.Sc) * 4};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
+            g.o == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSpec& g, const OutMap* Cg, int ncg,
                   cudaStream_t s, int* dstatus) {
   if (g.nreg <= 0) return;
-  if (g.o != 16 || g.oo != 256 || (g.kind != 1 && g.kind != 2) || !Cg[0].dst32) {
-    set_error("gemm_grouped: nocc 16 and an FP32 W chunk only");
+  if ((g.o != 16 && g.o != 32) || g.oo != g.o * g.o || g.ncol != g.oo / 256 || g.cblk != 256 / g.o ||
+      (g.kind != 1 && g.kind != 2) || !Cg[0].dst32) {
+    set_error("gemm_grouped: nocc 16 or 32 and an FP32 W chunk only");
     return;
   }
   using Cfg = TcCfg<256>;
@@ -1342,9 +1422,12 @@ void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSp
     }
   }
   CUtensorMap w0, w1;
-  const cuuint32_t box_a0[5] = {16, 2, 16, 2, 1}, box_a1[5] = {16, 16, 2, 2, 1}, box_b[5] = {16, 16, 2, 1, 2};
-  if (!make_wmap(&w0, Cg[0].dst32, g, g.kind == 1 ? box_a0 : box_b) ||
-      !make_wmap(&w1, Cg[0].dst32, g, g.kind == 1 ? box_a1 : box_b)) {
+  // boxes (j, k, i, a, c) of the epilogue's 32 x 32 blocks (see grp_epilogue / grp_epilogue32)
+  const cuuint32_t box16_a0[5] = {16, 2, 16, 2, 1}, box16_a1[5] = {16, 16, 2, 2, 1}, box16_b[5] = {16, 16, 2, 1, 2};
+  const cuuint32_t box32_a0[5] = {32, 1, 32, 1, 1}, box32_a1[5] = {32, 32, 1, 1, 1}, box32_b[5] = {32, 32, 1, 1, 1};
+  const cuuint32_t* b0 = g.o == 16 ? (g.kind == 1 ? box16_a0 : box16_b) : (g.kind == 1 ? box32_a0 : box32_b);
+  const cuuint32_t* b1 = g.o == 16 ? (g.kind == 1 ? box16_a1 : box16_b) : (g.kind == 1 ? box32_a1 : box32_b);
+  if (!make_wmap(&w0, Cg[0].dst32, g, b0) || !make_wmap(&w1, Cg[0].dst32, g, b1)) {
     set_error("cuTensorMapEncodeTiled failed (W chunk)");
     return;
   }

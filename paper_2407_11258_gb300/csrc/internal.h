@@ -111,6 +111,7 @@ struct GrpSpec {
   int Ma;            // valid rows of the problem: (b + 1) o (kind 1) or (b + 1) o^2 (kind 2)
   int nkb;           // K blocks of one term (Kp / 64)
   int c0, nc, cblk;  // the chunk's first c, its number of c, c values per column block (kind 2)
+  int ncol;          // kind 1: 256-column tiles per term (o^2 / 256: 1 at nocc 16, 4 at nocc 32)
   int b, bvo, vo, oo, o;  // slab b, b v o, v o, o^2, o
   long long Sc;      // W elements per c in the chunk
 };

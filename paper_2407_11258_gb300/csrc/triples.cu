@@ -149,8 +149,8 @@ __global__ void k_t_energy(const TW* __restrict__ W, long long slot_stride, int 
 // and every distinct ordering of (a, b, c); the i-sums are accumulated in Real and the block sum in FP64.
 // VFLY: only w is staged and v = w + disc s is recomputed where it is read (the slices, t1 columns and
 // d_m are in shared memory already); half the shared memory, for blocks too large to stage both.
-// Launched for the FP64 path and for the mixed path's VFLY blocks; the mixed path with both w and v
-// staged runs k_t_energy_f32 below.
+// Launched for the FP64 path; the mixed path runs k_t_energy_f32 (w and v staged) or k_t_energy_vfly
+// (w staged) below.
 template <typename TW, typename Real, int NLO, bool VFLY>
 __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
                                   const double* __restrict__ eps, const double* __restrict__ t1,
@@ -561,6 +561,209 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
   }
 }
 
+// Block energy of the mixed path when only w fits in shared memory (nocc 29..35 at 200 KB): w = W s is
+// staged, v = w + disc s is formed where it is read. s depends on the unordered triple (i, j, k), so one
+// rsqrt per (i, j, k) serves all six placements; of the fifteen slice / t1 values the six placements'
+// disconnected terms need at fixed (j, k), the ones that do not involve i stay in registers across the
+// i walk. Orderings are paired as in k_t_energy_f32 when a < b < c. 512 threads per block (two (j, k)
+// pairs per thread at nocc 32) with NLO <= 2, 256 above.
+template <int NLO>
+__global__ void __launch_bounds__(NLO <= 2 ? 512 : 256, 1)
+    k_t_energy_vfly(const float* __restrict__ W, long long slot_stride, int b, int c0, int o, int v,
+                    const double* __restrict__ eps, const double* __restrict__ t1, const float* __restrict__ ovT,
+                    const double* __restrict__ U, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int slot = blockIdx.y, a = blockIdx.x;
+  const int c = c0 + slot;
+  const long long blk_id = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
+  const int o2 = o * o, o3 = o2 * o;
+  const int S1 = o + 1, S0 = o * S1 + 1;
+  const int blk = o * S0;
+  float* sw = reinterpret_cast<float*>(smraw);  // w at y0 * S0 + y1 * S1 + y2
+  float* fs = sw + blk;
+  const int P1 = o + 1, o2p = o * P1;
+  float* Sab = fs;  // (y0 a|y1 b)
+  float* Sac = Sab + o2p;
+  float* Sbc = Sac + o2p;
+  float* ta = Sbc + o2p;
+  float* tb = ta + o;
+  float* tc = tb + o;
+  float* dm = tc + o;
+  const int uoff = (blk + 3 * o2p + 4 * o + 3) & ~3;
+  float* U2 = sw + uoff;  // (U[i][al], U[i][al]) pairs
+  const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
+  const float* oab = ovT + (1LL * a * v + b) * o2;
+  const float* oac = ovT + (1LL * a * v + c) * o2;
+  const float* obc = ovT + (1LL * b * v + c) * o2;
+  for (int idx = threadIdx.x; idx < o2; idx += blockDim.x) {
+    const int p = idx / o, q = idx % o;
+    Sab[p * P1 + q] = oab[idx];
+    Sac[p * P1 + q] = oac[idx];
+    Sbc[p * P1 + q] = obc[idx];
+  }
+  for (int y = threadIdx.x; y < o; y += blockDim.x) {
+    ta[y] = static_cast<float>(t1[y * v + a]);
+    tb[y] = static_cast<float>(t1[y * v + b]);
+    tc[y] = static_cast<float>(t1[y * v + c]);
+    dm[y] = static_cast<float>(ex3 - eps[y]);
+  }
+  for (int idx = threadIdx.x; idx < o * NLO; idx += blockDim.x) {
+    const float u = static_cast<float>(U[idx]);
+    U2[2 * idx] = u;
+    U2[2 * idx + 1] = u;
+  }
+  __syncthreads();
+  const float* Wb = W + slot * slot_stride + static_cast<long long>(a) * o3;
+  // staging: thread-owned (j, k) pairs walking i, as in k_t_energy_f32 (w only)
+  constexpr int kLoads = 8;
+  for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
+    const int y1 = jk % o, y2 = jk / o;
+    const float d12 = dm[y1] + dm[y2];
+    const float* wp = Wb + jk;
+    float* dst = sw + y1 * S1 + y2;
+    for (int i0 = 0; i0 < o; i0 += kLoads) {
+      float wr[kLoads];
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) wr[u] = i0 + u < o ? wp[static_cast<long long>(i0 + u) * o2] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u)
+        if (i0 + u < o) dst[(i0 + u) * S0] = wr[u] * rsqrtf(dm[i0 + u] + d12);
+    }
+  }
+  __syncthreads();
+  constexpr int PM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int x0 = a, x1 = b, x2 = c;
+  auto X = [&](int p) { return p == 0 ? x0 : (p == 1 ? x1 : x2); };
+  auto SS = [&](int p) { return p == 0 ? S0 : (p == 1 ? S1 : 1); };
+  const bool distinct = a < b && b < c;
+  bool act[6];
+#pragma unroll
+  for (int pi = 0; pi < 6; ++pi) {
+    bool dup = false;
+    if (!distinct) {
+#pragma unroll
+      for (int q = 0; q < pi; ++q)
+        dup = dup || (X(PM[q][0]) == X(PM[pi][0]) && X(PM[q][1]) == X(PM[pi][1]) && X(PM[q][2]) == X(PM[pi][2]));
+    }
+    act[pi] = !dup;
+  }
+  constexpr int NL = NLO > 0 ? NLO : 1;
+  double r_can = 0, r_frag = 0;  // FP32 sums over one (j, k); partials across (j, k) in FP64
+  for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
+    const int j = jk / o, k = jk % o;
+    int off[6], si[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      off[q] = j * SS(PM[q][1]) + k * SS(PM[q][2]);
+      si[q] = SS(PM[q][0]);
+    }
+    // (j, k)-only factors of the disconnected terms d(y0,y1,y2) = Sab[y0][y1] tc[y2] + Sac[y0][y2] tb[y1]
+    // + Sbc[y1][y2] ta[y0] of the placements (i,j,k), (i,k,j), (j,i,k), (k,i,j), (j,k,i), (k,j,i)
+    const float sbc_jk = Sbc[j * P1 + k], sbc_kj = Sbc[k * P1 + j], sac_jk = Sac[j * P1 + k],
+                sac_kj = Sac[k * P1 + j], sab_jk = Sab[j * P1 + k], sab_kj = Sab[k * P1 + j];
+    const float taj = ta[j], tak = ta[k], tbj = tb[j], tbk = tb[k], tcj = tc[j], tck = tc[k];
+    const float djk = dm[j] + dm[k];
+    float acc = 0.f;
+    float2 zy[6][NL];
+#pragma unroll
+    for (int h = 0; h < 6; ++h)
+#pragma unroll
+      for (int al = 0; al < NL; ++al) zy[h][al] = make_float2(0.f, 0.f);
+    for (int i = 0; i < o; ++i) {
+      float w[6], vv[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        w[q] = sw[off[q]];
+        off[q] += si[q];
+      }
+      const float s = rsqrtf(dm[i] + djk);
+      const float sab_ij = Sab[i * P1 + j], sab_ji = Sab[j * P1 + i], sab_ik = Sab[i * P1 + k],
+                  sab_ki = Sab[k * P1 + i];
+      const float sac_ij = Sac[i * P1 + j], sac_ji = Sac[j * P1 + i], sac_ik = Sac[i * P1 + k],
+                  sac_ki = Sac[k * P1 + i];
+      const float sbc_ij = Sbc[i * P1 + j], sbc_ji = Sbc[j * P1 + i], sbc_ik = Sbc[i * P1 + k],
+                  sbc_ki = Sbc[k * P1 + i];
+      const float tai = ta[i], tbi = tb[i], tci = tc[i];
+      vv[0] = w[0] + (sab_ij * tck + sac_ik * tbj + sbc_jk * tai) * s;  // (i, j, k)
+      vv[1] = w[1] + (sab_ik * tcj + sac_ij * tbk + sbc_kj * tai) * s;  // (i, k, j)
+      vv[2] = w[2] + (sab_ji * tck + sac_jk * tbi + sbc_ik * taj) * s;  // (j, i, k)
+      vv[3] = w[3] + (sab_ki * tcj + sac_kj * tbi + sbc_ij * tak) * s;  // (k, i, j)
+      vv[4] = w[4] + (sab_jk * tci + sac_ji * tbk + sbc_ki * taj) * s;  // (j, k, i)
+      vv[5] = w[5] + (sab_kj * tci + sac_ki * tbj + sbc_ji * tak) * s;  // (k, j, i)
+      float2 u2[NL];
+      if constexpr (NLO == 1) {
+        u2[0] = reinterpret_cast<const float2*>(U2)[i];
+      } else if constexpr (NLO > 1) {
+#pragma unroll
+        for (int h = 0; h < NLO / 2; ++h) {
+          const float4 t = reinterpret_cast<const float4*>(U2)[i * (NLO / 2) + h];
+          u2[2 * h] = make_float2(t.x, t.y);
+          u2[2 * h + 1] = make_float2(t.z, t.w);
+        }
+      }
+      if (distinct) {
+        // pairs (0, 5), (3, 1), (4, 2): (z_q - z_r, y_q), see k_t_energy_f32
+        const float dS = (w[0] + w[3] + w[4]) - (w[1] + w[2] + w[5]);
+        const float2 d0 = make_float2(fmaf(3.f, w[0] - w[5], dS), vv[0] - vv[5]);
+        const float2 d1 = make_float2(fmaf(3.f, w[3] - w[1], dS), vv[3] - vv[1]);
+        const float2 d2 = make_float2(fmaf(3.f, w[4] - w[2], dS), vv[4] - vv[2]);
+        acc = fmaf(d0.x, d0.y, acc);
+        acc = fmaf(d1.x, d1.y, acc);
+        acc = fmaf(d2.x, d2.y, acc);
+#pragma unroll
+        for (int al = 0; al < NLO; ++al) {
+          zy[0][al] = __ffma2_rn(u2[al], d0, zy[0][al]);
+          zy[1][al] = __ffma2_rn(u2[al], d1, zy[1][al]);
+          zy[2][al] = __ffma2_rn(u2[al], d2, zy[2][al]);
+        }
+      } else {
+#pragma unroll
+        for (int pi = 0; pi < 6; ++pi) {
+          if (!act[pi]) continue;
+          const int p0 = PM[pi][0], p1 = PM[pi][1], p2 = PM[pi][2];
+          auto idx = [&](int s0, int s1) {
+            return s0 == 0 ? (s1 == 1 ? 0 : 1) : (s0 == 1 ? (s1 == 0 ? 2 : 3) : (s1 == 0 ? 4 : 5));
+          };
+          const float z = 4 * w[idx(p0, p1)] + w[idx(p1, p2)] + w[idx(p2, p0)];
+          const float y = vv[idx(p0, p1)] - vv[idx(p2, p1)];
+          acc += z * y;
+          const float2 zyv = make_float2(z, y);
+#pragma unroll
+          for (int al = 0; al < NLO; ++al) zy[pi][al] = __ffma2_rn(u2[al], zyv, zy[pi][al]);
+        }
+      }
+    }
+    r_can += static_cast<double>(acc);
+    float f = 0.f;
+#pragma unroll
+    for (int pi = 0; pi < 6; ++pi)
+#pragma unroll
+      for (int al = 0; al < NLO; ++al) f += zy[pi][al].x * zy[pi][al].y;
+    r_frag += static_cast<double>(f);
+  }
+  double e_can = r_can, e_frag = r_frag;
+  __shared__ double sh[2][32];
+  for (int offs = 16; offs > 0; offs >>= 1) {
+    e_can += __shfl_xor_sync(0xffffffffu, e_can, offs);
+    e_frag += __shfl_xor_sync(0xffffffffu, e_frag, offs);
+  }
+  const int wi = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) {
+    sh[0][wi] = e_can;
+    sh[1][wi] = e_frag;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
+      s0 += sh[0][q];
+      s1 += sh[1][q];
+    }
+    out[2 * blk_id] = -s0 / 3.0;
+    out[2 * blk_id + 1] = -s1 / 3.0;
+  }
+}
+
 // FP32 copy of (ia|jb) in the order the block energy reads it: ovT[a][b][i][j] = (ia|jb).
 __global__ void k_ovov_t(const double* __restrict__ ovov, float* __restrict__ ovT, int o, int v) {
   const long long ov = 1LL * o * v, n = ov * ov, oo = 1LL * o * o;
@@ -870,8 +1073,8 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     cudaMemsetAsync(dUp, 0, static_cast<size_t>(o) * nlo_t * 8, s);
     cudaMemcpy2DAsync(dUp, nlo_t * 8, U, nlo * 8, nlo * 8, o, cudaMemcpyDeviceToDevice, s);
   }
-  float* ovT = nullptr;  // k_t_energy_f32 reads (ia|jb) from this FP32 copy
-  if (bf && staged && staged_full) {
+  float* ovT = nullptr;  // k_t_energy_f32 / k_t_energy_vfly read (ia|jb) from this FP32 copy
+  if (bf && staged) {
     ovT = static_cast<float*>(tmp_alloc(tp.ovt));
     if (!ovT) {
       cleanup();
@@ -895,9 +1098,8 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
         k_t_energy_f32<K, 0><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, v, eps,  \
                                                       t1, ovT, dUp, part);                               \
     else                                                                                                 \
-      k_t_energy_staged<float, float, K, true><<<grid, 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, \
-                                                                        c0, o, v, eps, t1, ovov, dUp,    \
-                                                                        nlo_t, part);                    \
+      k_t_energy_vfly<K><<<grid, K <= 2 ? 512 : 256, esmem, s>>>(static_cast<const float*>(Wp), Sc, b, c0, o, \
+                                                                 v, eps, t1, ovT, dUp, part);            \
   } while (0)
 #define LN_D(K)                                                                                          \
   do {                                                                                                   \
@@ -954,11 +1156,11 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 4, false>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 8, false>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 0, true>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 1, true>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 2, true>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 4, true>));
-      attr(reinterpret_cast<const void*>(k_t_energy_staged<float, float, 8, true>));
+      attr(reinterpret_cast<const void*>(k_t_energy_vfly<0>));
+      attr(reinterpret_cast<const void*>(k_t_energy_vfly<1>));
+      attr(reinterpret_cast<const void*>(k_t_energy_vfly<2>));
+      attr(reinterpret_cast<const void*>(k_t_energy_vfly<4>));
+      attr(reinterpret_cast<const void*>(k_t_energy_vfly<8>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 0, true>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 1, true>));
       attr(reinterpret_cast<const void*>(k_t_energy_staged<double, double, 2, true>));
@@ -972,9 +1174,9 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     return m;
   };
   const int o2 = static_cast<int>(oo);
-  // grouped launches (two per chunk instead of five) where one accumulator holds a (y, z) plane and
-  // 128-row tiles hold whole a values
-  const bool grouped = bf && o == 16 && opts.triples_kernel != LNOCC_TK_PER_TERM;
+  // grouped launches (two per chunk instead of five) where 128-row tiles hold whole a values (kind 1)
+  // and a (y, z) plane is one (nocc 16) or four (nocc 32) 256-column accumulator tiles
+  const bool grouped = bf && (o == 16 || o == 32) && opts.triples_kernel != LNOCC_TK_PER_TERM;
   const Packed* ops_a[4] = {&XT1, &TO, &XT2, &TOT};
   const Packed* ops_b[4] = {&TO, &XT2, &TO, &XT1};
   const int box_ab[4] = {128, 256, 128, 256};
@@ -1003,6 +1205,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       g.c0 = c0;
       g.nc = nc;
       g.cblk = 256 / o;
+      g.ncol = o2 / 256;
       g.b = b;
       g.bvo = xb;
       g.vo = v * o;

@@ -200,6 +200,22 @@ def test_triples_grouped_launches(lnocc):
             assert abs(res[1, mb][k] - res[2, mb][k]) < 1e-9, (mb, k)
 
 
+def test_triples_grouped_launches_nocc32(lnocc):
+    """nocc=32: the grouped launches with four 256-column tiles per (y, z) plane and 32 x 32 W boxes
+    (128-byte swizzle). Both launch forms against the live oracle, default and 1 MB chunks."""
+    fr = synth.make_fragment(32, 16, 64, 3216, decay=20.0, frag=(0, 1))
+    ref = oracle_solve(fr)
+    res = {}
+    for tk in (lnocc.LNOCC_TK_PER_TERM, lnocc.LNOCC_TK_GROUPED):
+        for mb in (0, 1):
+            got = gpu_solve(lnocc, fr, 1, triples_kernel=tk, triples_chunk_mb=mb)
+            assert_parity(got, ref, MIXED_TOL)
+            res[tk, mb] = got
+    for mb in (0, 1):
+        for k in ("e_t", "e_t_frag"):
+            assert abs(res[1, mb][k] - res[2, mb][k]) < 1e-9, (mb, k)
+
+
 # ------------------------------------------------------------------ properties
 
 def test_deterministic_repeat(lnocc):
