@@ -27,6 +27,8 @@
  *     lnocc_workspace_bytes(...) bytes: from a workspace the caller attached with lnocc_frag_set_workspace
  *     (then it allocates nothing), else it allocates and frees them itself within the call. The other
  *     allocating calls say so (the diagnostic GEMM, the batch runtime, MLP handles, autotuner mode 2).
+ *     A handle's allocations come from the library's cached stream-ordered pool (opts.memory, default
+ *     LNOCC_MEM_CACHED), which keeps freed memory for later handles; lnocc_trim_pool returns it.
  */
 #ifndef LNOCC_H
 #define LNOCC_H
