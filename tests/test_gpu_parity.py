@@ -216,6 +216,18 @@ def test_triples_grouped_launches_nocc32(lnocc):
             assert abs(res[1, mb][k] - res[2, mb][k]) < 1e-9, (mb, k)
 
 
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_two_electron_fragment(lnocc, prec, tol):
+    """nocc = 1 (two electrons): CCSD is exact (it equals the oracle, which is pinned by FCI for this
+    case) and (T) vanishes identically: with one occupied orbital every W block is symmetric in its
+    virtual labels, so each v - v' term is a difference of equal values (exactly zero on both paths)."""
+    fr = synth.make_fragment(1, 23, 92, 4101, decay=20.0, frag=(0,))
+    ref = oracle_solve(fr, do_t=False)
+    got = gpu_solve(lnocc, fr, prec)
+    assert_parity(got, ref, tol)
+    assert got["e_t"] == 0.0 and got["e_t_frag"] == 0.0
+
+
 # ------------------------------------------------------------------ properties
 
 def test_deterministic_repeat(lnocc):
