@@ -191,6 +191,24 @@ int lnocc_triples(lnocc_frag* f, int nlo, const double* U_frag, double* e_t_full
                   void* stream);
 
 /*
+ * Graph-capturable forms (device-pointer outputs). They enqueue the same work on `stream` as
+ * lnocc_fragment_energy / lnocc_triples and return without synchronising: no host-side wait, no
+ * timing events, no device allocation, no tile timing. The results are written to DEVICE memory when
+ * the stream reaches them, so either call may be captured into a CUDA graph (stream capture) and
+ * replayed; the handle's amplitudes are read when the work runs.
+ *   lnocc_fragment_energy_device: e_dev[0] = E_CCSD^(F), e_dev[1] = E_MP2^(F) (Eq. 12-13).
+ *   lnocc_triples_device: needs a workspace attached with lnocc_frag_set_workspace (LNOCC_EINVAL
+ *     otherwise); e_dev[0] = E_(T), e_dev[1] = E_(T)^(F) (0 when U_frag is NULL); status_dev (device
+ *     int, may be NULL) receives the device status word of the call: 0, or a nonzero code when a bounded
+ *     wait of a contraction kernel ran out (the host-synchronous call reports that as LNOCC_ETIMEOUT).
+ * Argument errors are reported at enqueue time as by the synchronous calls; a non-finite energy is
+ * not checked (it is in e_dev).
+ */
+int lnocc_fragment_energy_device(lnocc_frag* f, int nlo, const double* U_frag, double* e_dev, void* stream);
+int lnocc_triples_device(lnocc_frag* f, int nlo, const double* U_frag, double* e_dev, int* status_dev,
+                         void* stream);
+
+/*
  * lnocc_workspace_bytes -- device scratch that lnocc_triples needs for a fragment of these sizes
  * (Sec. II.D's (T) step: packed W/V operands, the W chunk and the block partial sums), for the precision
  * and opts->triples_chunk_mb of `opts` (NULL: defaults). *bytes receives the size.

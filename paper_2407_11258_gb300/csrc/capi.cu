@@ -160,6 +160,32 @@ int lnocc_triples(lnocc_frag* h, int nlo, const double* U_frag, double* e_t_full
   return h->f.triples(U_frag ? nlo : 0, U_frag, e_t_full, e_t_frag);
 }
 
+int lnocc_fragment_energy_device(lnocc_frag* h, int nlo, const double* U_frag, double* e_dev, void* stream) {
+  lnocc::set_error("");
+  if (!h || nlo < 1 || !U_frag || !e_dev) {
+    lnocc::set_error("lnocc_fragment_energy_device: bad arguments");
+    return LNOCC_EINVAL;
+  }
+  h->f.s = static_cast<cudaStream_t>(stream);
+  h->f.use_workspace();
+  return h->f.fragment_energy(nlo, U_frag, nullptr, nullptr, e_dev);
+}
+
+int lnocc_triples_device(lnocc_frag* h, int nlo, const double* U_frag, double* e_dev, int* status_dev, void* stream) {
+  lnocc::set_error("");
+  if (!h || (U_frag && nlo < 1) || !e_dev) {
+    lnocc::set_error("lnocc_triples_device: bad arguments");
+    return LNOCC_EINVAL;
+  }
+  if (!h->f.have_amps) {
+    lnocc::set_error("lnocc_triples_device: no CCSD amplitudes (call lnocc_ccsd first)");
+    return LNOCC_EINVAL;
+  }
+  h->f.s = static_cast<cudaStream_t>(stream);
+  h->f.use_workspace();
+  return h->f.triples(U_frag ? nlo : 0, U_frag, nullptr, nullptr, e_dev, status_dev);
+}
+
 int lnocc_workspace_bytes(int nocc, int nvir, int naux, const lnocc_opts* opts, long long* bytes) {
   lnocc::set_error("");
   lnocc_opts o;

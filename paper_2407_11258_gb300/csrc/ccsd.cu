@@ -884,10 +884,10 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
 }
 
 // Pair matrix E_ii' = sum_jab tau_ij^ab L[i'][j][a][b] (FP64), then the LO projection.
-int Frag::fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double* e_mp2_frag) {
+int Frag::fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double* e_mp2_frag, double* e_dev) {
   const long long ov = 1LL * o * v;
   const long long kk = ov * v;  // (j,a,b)
-  auto pair_and_project = [&](const double* t1, const double* t2, double* out_host) -> int {
+  auto pair_and_project = [&](const double* t1, const double* t2, double* out_host, double* out_dev) -> int {
     if (t1) {
       launch_tau(t1, t2, tau, o, v, s);
     } else {
@@ -895,21 +895,34 @@ int Frag::fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double*
     }
     launch_pair_dots(tau, Lpair, o, kk, Eii, s);
     launch_project(Eii, U, o, nlo, scal + 2, s);
+    if (out_dev) {
+      LN_CUDA(cudaMemcpyAsync(out_dev, scal + 2, 8, cudaMemcpyDeviceToDevice, s));
+      return LNOCC_OK;
+    }
     LN_CUDA(cudaMemcpyAsync(h_scal + 2, scal + 2, 8, cudaMemcpyDeviceToHost, s));
     LN_CUDA(cudaStreamSynchronize(s));
     *out_host = h_scal[2];
     return LNOCC_OK;
   };
+  if (e_dev) {
+    if (!have_amps) {
+      set_error("lnocc_fragment_energy_device: no CCSD amplitudes (call lnocc_ccsd first)");
+      return LNOCC_EINVAL;
+    }
+    const int st = pair_and_project(xcur, xcur + ov, nullptr, e_dev);
+    if (st) return st;
+    return pair_and_project(nullptr, t2mp2, nullptr, e_dev + 1);
+  }
   if (e_ccsd_frag) {
     if (!have_amps) {
       set_error("lnocc_fragment_energy: no CCSD amplitudes (call lnocc_ccsd first)");
       return LNOCC_EINVAL;
     }
-    const int st = pair_and_project(xcur, xcur + ov, e_ccsd_frag);
+    const int st = pair_and_project(xcur, xcur + ov, e_ccsd_frag, nullptr);
     if (st) return st;
   }
   if (e_mp2_frag) {
-    const int st = pair_and_project(nullptr, t2mp2, e_mp2_frag);
+    const int st = pair_and_project(nullptr, t2mp2, e_mp2_frag, nullptr);
     if (st) return st;
   }
   return check_device();

@@ -132,8 +132,10 @@ struct Frag {
   void iterate(bool fp64_residual);
   double energy_of(const double* x);
   int solve(int guess, const double* t1_in, const double* t2_in);
-  int fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double* e_mp2_frag);
-  int triples(int nlo, const double* U, double* e_full, double* e_frag);
+  // e_dev (device, 2 doubles) set: enqueue only, results copied there (graph-capturable forms)
+  int fragment_energy(int nlo, const double* U, double* e_ccsd_frag, double* e_mp2_frag, double* e_dev = nullptr);
+  int triples(int nlo, const double* U, double* e_full, double* e_frag, double* e_dev = nullptr,
+              int* st_dev = nullptr);
 };
 
 }  // namespace lnocc

@@ -764,6 +764,29 @@ __global__ void __launch_bounds__(NLO <= 2 ? 512 : 256, 1)
   }
 }
 
+// Per-c tables of the batched (T) terms, one entry per (b, c >= b) in b-major order (the order of the
+// chunk plan: entry (b, c) at b v - b (b - 1) / 2 + c - b). For W chunks of ncmax(b) = max(1, welems /
+// ((b + 1) o^3)) values of c, c sits at position q = (c - b) mod ncmax(b) of its chunk. bat: sigma5
+// (rows (c, a, k) of XT2 against rows (b, i, j) of TOT); bat12: sigma1 (rows (b, a, i) of XT1 against rows
+// (c, k, j) of TO) then sigma2 (rows (c, a, i) of XT1 against rows (b, k, j) of TOT) into one accumulator.
+__global__ void k_batch_tables(int o, int v, long long welems, BatchEntry* __restrict__ bat,
+                               BatchEntry* __restrict__ bat12) {
+  const long long oo = 1LL * o * o, ooo = oo * o;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < v; b += gridDim.x * blockDim.x) {
+    const long long slab = 1LL * (b + 1) * ooo;
+    const long long ncmax = welems / slab > 1 ? welems / slab : 1;
+    const long long base = 1LL * b * v - 1LL * b * (b - 1) / 2;
+    const int Ma = (b + 1) * o;
+    const int brow = b * static_cast<int>(oo);
+    for (int c = b; c < v; ++c) {
+      const long long q = (c - b) % ncmax;
+      const int arow = c * v * o;
+      bat[base + c - b] = BatchEntry{arow, brow, Ma, arow, brow, 0, q * slab};
+      bat12[base + c - b] = BatchEntry{b * v * o, c * static_cast<int>(oo), Ma, arow, brow, 0, q * slab};
+    }
+  }
+}
+
 // FP32 copy of (ia|jb) in the order the block energy reads it: ovT[a][b][i][j] = (ia|jb).
 __global__ void k_ovov_t(const double* __restrict__ ovov, float* __restrict__ ovT, int o, int v) {
   const long long ov = 1LL * o * v, n = ov * ov, oo = 1LL * o * o;
@@ -893,25 +916,44 @@ TriplesPlan triples_plan(int o, int v, int N, bool bf, int chunk_mb) {
   return p;
 }
 
-int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
+int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag, double* e_dev, int* st_dev) {
   const long long oo = 1LL * o * o, vv = 1LL * v * v, ov = 1LL * o * v, ooo = oo * o;
   const bool bf = mixed;
-  cudaMemsetAsync(dstatus, 0, 16 * 4, s);
-  const double* t1 = xcur;
-  const double* t2 = xcur + ov;
-  cudaEvent_t ev_call0, ev_call1;
-  cudaEventCreate(&ev_call0);
-  cudaEventCreate(&ev_call1);
-  cudaEventRecord(ev_call0, s);
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // around each chunk's contraction launches
-
-  // ---- operands (packed once per call)
+  // device-output mode: enqueue only (no host synchronisation, no event timing, no allocation, no
+  // tile timing), so that the call can be captured into a CUDA graph; the energies and the device
+  // status word are copied to the caller's device memory at the end of the stream's work
+  const bool dev_out = e_dev != nullptr;
   const TriplesPlan tp = triples_plan(o, v, N, bf, opts.triples_chunk_mb);
   if (ws_ext && ws_ext_bytes < tp.total) {
     set_error("lnocc_triples: attached workspace smaller than lnocc_workspace_bytes (" + std::to_string(tp.total) +
               " bytes)");
     return LNOCC_EINVAL;
   }
+  if (dev_out && !ws_ext) {
+    set_error("lnocc_triples_device: attach a workspace first (lnocc_frag_set_workspace)");
+    return LNOCC_EINVAL;
+  }
+  struct TimingGuard {  // no tile timing (it synchronises and allocates) in device-output mode
+    bool saved, active;
+    explicit TimingGuard(bool on) : saved(autotune_timing_allowed()), active(on) {
+      if (active) autotune_timing_allowed() = false;
+    }
+    ~TimingGuard() {
+      if (active) autotune_timing_allowed() = saved;
+    }
+  } timing_guard(dev_out);
+  cudaMemsetAsync(dstatus, 0, 16 * 4, s);
+  const double* t1 = xcur;
+  const double* t2 = xcur + ov;
+  cudaEvent_t ev_call0 = nullptr, ev_call1 = nullptr;
+  if (!dev_out) {
+    cudaEventCreate(&ev_call0);
+    cudaEventCreate(&ev_call1);
+    cudaEventRecord(ev_call0, s);
+  }
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;  // around each chunk's contraction launches
+
+  // ---- operands (packed once per call)
   std::vector<void*> mine;
   size_t ws_used = 0;
   // temporaries: carved in plan order from the caller's workspace when one is attached (no device
@@ -929,8 +971,11 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     return p;
   };
   auto cleanup = [&]() {
-    cudaStreamSynchronize(s);
+    if (!dev_out) cudaStreamSynchronize(s);
     for (void* p : mine) dev_free(p);
+    if (ev_call0) cudaEventDestroy(ev_call0);
+    if (ev_call1) cudaEventDestroy(ev_call1);
+    ev_call0 = ev_call1 = nullptr;
   };
   auto mk = [&](int rows, int K) -> Packed {
     Packed P;
@@ -1015,7 +1060,7 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     long long tab, part;
   };
   std::vector<Chunk> plan;
-  std::vector<BatchEntry> hbat, hbat12;  // per-c tables: sigma5 (and rows for sigma2) / merged sigma1 + sigma2
+  long long ntab = 0;  // entries of the per-c tables: one per (b, c >= b), b-major
   {
     long long part = 0;
     for (int b = 0; b < v; ++b) {
@@ -1023,23 +1068,15 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       const int ncmax = static_cast<int>(std::max(1LL, welems / slab));
       for (int c0 = b; c0 < v; c0 += ncmax) {
         const int nc = std::min(ncmax, v - c0);
-        plan.push_back(Chunk{b, c0, nc, static_cast<long long>(hbat.size()), part});
-        const int Ma = (b + 1) * o;
-        for (int q = 0; q < nc; ++q) {
-          const int arow = (c0 + q) * v * o;           // rows (c, a, .) of X1 / T2x / X2 / T2y
-          const int brow = b * static_cast<int>(oo);  // rows (b, ., .) of TvT / O1T / Tv / O1
-          hbat.push_back(BatchEntry{arow, brow, Ma, arow, brow, 0, q * slab});
-          // sigma1 (rows (b, a, i) of XT1 against rows (c, k, j) of TO) then sigma2 (rows (c, a, i) of XT1
-          // against rows (b, k, j) of TOT): the same (a,i) x (k,j) block of W[c], one accumulator
-          hbat12.push_back(BatchEntry{b * v * o, (c0 + q) * static_cast<int>(oo), Ma, arow, brow, 0, q * slab});
-        }
+        plan.push_back(Chunk{b, c0, nc, ntab, part});
+        ntab += nc;
         part += 1LL * (b + 1) * nc;
       }
     }
   }
   BatchEntry* dbat = static_cast<BatchEntry*>(tmp_alloc(tp.batch));
   BatchEntry* dbat12 = static_cast<BatchEntry*>(tmp_alloc(tp.batch));
-  if (sizeof(BatchEntry) * hbat.size() > tp.batch || sizeof(BatchEntry) * hbat12.size() > tp.batch) {
+  if (sizeof(BatchEntry) * static_cast<size_t>(ntab) > tp.batch) {
     cleanup();
     set_error("lnocc_triples: internal error (launch tables larger than planned)");
     return LNOCC_EINVAL;
@@ -1049,8 +1086,8 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     set_error("lnocc_triples: device allocation failed (W chunk)");
     return LNOCC_ENOMEM;
   }
-  cudaMemcpyAsync(dbat, hbat.data(), sizeof(BatchEntry) * hbat.size(), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(dbat12, hbat12.data(), sizeof(BatchEntry) * hbat12.size(), cudaMemcpyHostToDevice, s);
+  count_launch();
+  k_batch_tables<<<(v + 127) / 128, 128, 0, s>>>(o, v, welems, dbat, dbat12);
 
   const long long sblk = 1LL * o * (1LL * o * (o + 1) + 1);  // padded w / v block of the energy kernel
   // slices, t1 columns, d_m and U (up to 8 LOs, duplicated into pairs, plus 16-byte alignment)
@@ -1189,10 +1226,12 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     const int na = b + 1, Ma = na * o, Ma2 = na * o2;
     const long long Sc = 1LL * na * ooo;  // W stride of c
     const int xb = b * v * o;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!dev_out) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
     // W layout [c - c0][a][i][k][j]; each term is one contraction over K = v + o (d-part, then l-part).
     if (grouped) {
       // launch 1, per (c, 128-row tile of (a, x)): sigma1 + sigma2 stored, then sigma3 and sigma5 added
@@ -1269,8 +1308,10 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
       gemm_batched(XT2, TOT, dbat + ch.tab, nc, Ma, o2, Kt, m, s, dstatus);
     }
     }
-    cudaEventRecord(e1, s);
-    gev.emplace_back(e0, e1);
+    if (!dev_out) {
+      cudaEventRecord(e1, s);
+      gev.emplace_back(e0, e1);
+    }
     if (staged) {
       energy_launch(W, Sc, b, c0, na, nc, tpart + 2 * ch.part);
     } else {
@@ -1290,6 +1331,18 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     k_t_finish_part<<<kParts, 1024, 0, s>>>(tpart, nblk_total, chunk, tpart + 2 * nblk_total);
     k_t_finish<<<1, 1024, 0, s>>>(tpart + 2 * nblk_total, kParts, scal + 4);
   }
+  if (dev_out) {
+    // E_T and E_T^(F) (zero without LOs: the kernels sum no projected terms then) and the status word
+    cudaMemcpyAsync(e_dev, scal + 4, 16, cudaMemcpyDeviceToDevice, s);
+    if (st_dev) cudaMemcpyAsync(st_dev, dstatus, 4, cudaMemcpyDeviceToDevice, s);
+    cleanup();
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+      set_error(std::string("lnocc_triples_device: ") + cudaGetErrorString(ce));
+      return LNOCC_ECUDA;
+    }
+    return LNOCC_OK;
+  }
   cudaMemcpyAsync(h_scal + 4, scal + 4, 16, cudaMemcpyDeviceToHost, s);
   cudaEventRecord(ev_call1, s);
   cudaStreamSynchronize(s);
@@ -1304,8 +1357,6 @@ int Frag::triples(int nlo, const double* U, double* e_full, double* e_frag) {
     }
     cudaEventElapsedTime(&ms, ev_call0, ev_call1);
     t_triples_ms = ms;
-    cudaEventDestroy(ev_call0);
-    cudaEventDestroy(ev_call1);
   }
   const int st = check_device();
   if (e_full) *e_full = h_scal[4];

@@ -34,7 +34,7 @@ EXPORTS = ["lnocc_default_opts", "lnocc_build_ints", "lnocc_ccsd", "lnocc_fragme
            "lnocc_mlp_forward", "lnocc_mlp_grad", "lnocc_mlp_guess", "lnocc_frag_set_mlp", "lnocc_mp2_workspace_bytes",
            "lnocc_mp2_energy", "lnocc_workspace_bytes", "lnocc_frag_set_workspace", "lnocc_debug_wait",
            "lnocc_lno_internal", "lnocc_lno_densities", "lnocc_lno_select", "lnocc_active_space",
-           "lnocc_kpoint_df", "lnocc_trim_pool"]
+           "lnocc_kpoint_df", "lnocc_trim_pool", "lnocc_fragment_energy_device", "lnocc_triples_device"]
 
 
 class Opts(ctypes.Structure):
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lnocc_frag_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lnocc_free_fragment.argtypes = [P]
     lib.lnocc_trim_pool.argtypes = []
+    lib.lnocc_fragment_energy_device.argtypes = [P, I, P, P, P]
+    lib.lnocc_triples_device.argtypes = [P, I, P, P, P, P]
     lib.lnocc_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
     lib.lnocc_default_batch_opts.restype = None
     lib.lnocc_solve_batch.argtypes = [I, ctypes.POINTER(BatchItem), ctypes.POINTER(Opts), ctypes.POINTER(BatchOpts),
@@ -291,6 +293,29 @@ def lnocc_triples(frag: Fragment, U_frag=None, stream=None):
     nlo = int(U_frag.shape[1]) if U_frag is not None else 0
     _check(load().lnocc_triples(frag.h, nlo, _ptr(U_frag), ctypes.byref(ef), ctypes.byref(eF), _stream(stream)))
     return ef.value, eF.value
+
+
+def lnocc_fragment_energy_device(frag: Fragment, U_frag, e_dev, stream=None):
+    """Enqueue the projected CCSD and MP2 energies into e_dev (float64 CUDA tensor of 2 elements) without
+    synchronising (graph-capturable)."""
+    _rows(U_frag, _dims(frag)[0])
+    _need(e_dev, 2, "e_dev")
+    _check(load().lnocc_fragment_energy_device(frag.h, int(U_frag.shape[1]), _ptr(U_frag), _ptr(e_dev),
+                                               _stream(stream)))
+
+
+def lnocc_triples_device(frag: Fragment, U_frag, e_dev, status_dev=None, stream=None):
+    """Enqueue the (T) energy and its projection into e_dev (float64 CUDA tensor of 2 elements) and the
+    device status word into status_dev (int32 CUDA tensor of 1 element, optional) without synchronising
+    (graph-capturable; needs an attached workspace)."""
+    import torch
+    _rows(U_frag, _dims(frag)[0])
+    _need(e_dev, 2, "e_dev")
+    _need(status_dev, 1, "status_dev")
+    nlo = int(U_frag.shape[1]) if U_frag is not None else 0
+    _check(load().lnocc_triples_device(frag.h, nlo, _ptr(U_frag), _ptr(e_dev),
+                                       _ptr(status_dev, torch.int32) if status_dev is not None else None,
+                                       _stream(stream)))
 
 
 def lnocc_workspace_bytes(nocc, nvir, naux, opts=None):

@@ -93,3 +93,51 @@ def test_workspace_size_follows_the_chunk_option_and_is_checked(lnocc):
     finally:
         f.free()
     assert np.isfinite(got["e_t"])
+
+
+@pytest.mark.parametrize("shape", [(16, 40, 160), (5, 37, 150)])
+def test_device_outputs_capture_into_a_cuda_graph(lnocc, shape):
+    """lnocc_fragment_energy_device and lnocc_triples_device enqueue without synchronising and write
+    device memory: captured into a CUDA graph and replayed they give the synchronous calls' energies
+    bit for bit. nocc=16 runs the grouped (T) launches, nocc=5 the per-term ones with device-built
+    launch tables."""
+    o, v, q = shape
+    fr = synth.make_fragment(o, v, q, 1700 + o, decay=20.0, frag=(0, 1))
+    eps, B, U = (torch.tensor(x, device="cuda") for x in (fr.eps, fr.B, fr.U_frag))
+    opts = lnocc.default_opts(precision=1)
+    f = lnocc.lnocc_build_ints(o, v, q, eps, B, opts)
+    try:
+        lnocc.lnocc_ccsd(f)
+        ec, em = lnocc.lnocc_fragment_energy(f, U)
+        et, etf = lnocc.lnocc_triples(f, U)
+        ws = torch.empty(lnocc.lnocc_workspace_bytes(o, v, q, opts), dtype=torch.uint8, device="cuda")
+        lnocc.lnocc_frag_set_workspace(f, ws)
+        e1 = torch.zeros(2, dtype=torch.float64, device="cuda")
+        e2 = torch.zeros(2, dtype=torch.float64, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        lnocc.lnocc_fragment_energy_device(f, U, e1, stream=s)  # eager enqueue
+        lnocc.lnocc_triples_device(f, U, e2, st, stream=s)
+        s.synchronize()
+        assert e1.tolist() == [ec, em] and e2.tolist() == [et, etf] and int(st.item()) == 0
+        e1.zero_()
+        e2.zero_()
+        st.fill_(-1)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            lnocc.lnocc_fragment_energy_device(f, U, e1, stream=s)
+            lnocc.lnocc_triples_device(f, U, e2, st, stream=s)
+        assert e2.tolist() == [0.0, 0.0]  # capture records the work, nothing has run yet
+        for _ in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            assert e1.tolist() == [ec, em] and e2.tolist() == [et, etf] and int(st.item()) == 0
+        with pytest.raises(lnocc.LnoccError) as ei:  # a workspace is required
+            lnocc.lnocc_frag_set_workspace(f, None)
+            lnocc.lnocc_triples_device(f, U, e2, st, stream=s)
+        assert ei.value.code == lnocc.LNOCC_EINVAL
+    finally:
+        torch.cuda.synchronize()
+        f.free()
