@@ -537,56 +537,60 @@ __global__ void k_e2_occ(const double* __restrict__ t2, const double* __restrict
 // conversions through the IEEE fields (no FP64-pipe work per element), the dressed factors stored as
 // FP64. One warp per row; the v-sums end in a fixed-order warp butterfly.
 template <int MAXO>
-__global__ void k_dress_vv(const double* __restrict__ Bvv, const double* __restrict__ Bov,
+__global__ void __launch_bounds__(256, 2) k_dress_vv(const double* __restrict__ Bvv, const double* __restrict__ Bov,
                            const double* __restrict__ t1, double* __restrict__ Bvv_h, double* __restrict__ Bvo_h,
                            int o, int v) {
+  // Rows of B_vv[Q] in chunks of kRows: each thread owns columns c (it keeps B_ov[Q][k][c] for its
+  // column in registers) and reads the chunk's kRows values of its column with all loads in flight;
+  // the chunk is kept (FP32) in shared memory for the B^_vo sums, one (a, k) per thread. Row strides of
+  // v + 1 floats keep the column-wise reads of t1 free of bank conflicts.
+  constexpr int kRows = 16;
   extern __shared__ float dsm[];
-  float* ts = dsm;                    // t1[k][c], o x v
-  float* bs = dsm + MAXO * v;         // B_ov[Q][k][c], o x v
+  const int vp = v + 1;
+  float* ts = dsm;              // t1[k][c], row stride vp
+  float* xs = dsm + MAXO * vp;  // the chunk's rows of B_vv[Q] (FP32), row stride vp
   const int Q = blockIdx.x;
   const long long ov = static_cast<long long>(o) * v, vv = static_cast<long long>(v) * v;
-  for (int x = threadIdx.x; x < o * v; x += blockDim.x) {
-    ts[x] = static_cast<float>(t1[x]);
-    bs[x] = static_cast<float>(Bov[Q * ov + x]);
+  // rows k >= nocc are zero (the unrolled k loops below read all MAXO rows)
+  for (int x = threadIdx.x; x < MAXO * v; x += blockDim.x) {
+    const int k = x / v, c = x % v;
+    ts[k * vp + c] = k < o ? f64_to_f32_fields(t1[x]) : 0.f;
   }
   __syncthreads();
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int a = warp; a < v; a += nw) {
-    float ta[MAXO], acc[MAXO];
+  const double* Bq = Bvv + Q * vv;
+  double* Hq = Bvv_h + Q * vv;
+  for (int a0 = 0; a0 < v; a0 += kRows) {
+    const int nr = min(kRows, v - a0);
+    for (int c = threadIdx.x; c < v; c += blockDim.x) {
+      float bk[MAXO];
 #pragma unroll
-    for (int k = 0; k < MAXO; ++k) {
-      ta[k] = k < o ? ts[k * v + a] : 0.f;
-      acc[k] = 0.f;
-    }
-    const double* row = Bvv + Q * vv + static_cast<long long>(a) * v;
-    double* orow = Bvv_h + Q * vv + static_cast<long long>(a) * v;
-    for (int c0 = lane; c0 < v; c0 += 32 * 8) {
-      double xs[8];  // eight independent loads in flight per lane
+      for (int k = 0; k < MAXO; ++k) bk[k] = k < o ? f64_to_f32_fields(Bov[Q * ov + 1LL * k * v + c]) : 0.f;
+      double xr[kRows];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) xs[t] = c0 + 32 * t < v ? row[c0 + 32 * t] : 0.0;
+      for (int r = 0; r < kRows; ++r) xr[r] = r < nr ? Bq[1LL * (a0 + r) * v + c] : 0.0;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int c = c0 + 32 * t;
-        if (c >= v) break;
-        const float xf = f64_to_f32_fields(xs[t]);
-        float corr = 0.f;
+      for (int r = 0; r < kRows; ++r) {
+        if (r < nr) {
+          const float xf = f64_to_f32_fields(xr[r]);
+          float corr = 0.f;
 #pragma unroll
-        for (int k = 0; k < MAXO; ++k)
-          if (k < o) {
-            corr = fmaf(ta[k], bs[k * v + c], corr);
-            acc[k] = fmaf(xf, ts[k * v + c], acc[k]);
-          }
-        orow[c] = f32_to_f64_fields(xf - corr);
+          for (int k = 0; k < MAXO; ++k) corr = fmaf(ts[k * vp + a0 + r], bk[k], corr);  // t_k^a B_ov[Q][k][c]
+          Hq[1LL * (a0 + r) * v + c] = f32_to_f64_fields(xf - corr);
+          xs[r * vp + c] = xf;
+        }
       }
     }
-#pragma unroll
-    for (int k = 0; k < MAXO; ++k)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-    double* vo = Bvo_h + Q * ov + static_cast<long long>(a) * o;
-#pragma unroll
-    for (int k = 0; k < MAXO; ++k)
-      if (k < o && lane == k) vo[k] += static_cast<double>(acc[k]);
+    __syncthreads();
+    // B^_vo[Q][a][k] += sum_c B_vv[Q][a][c] t_k^c for the chunk's rows (fixed summation order over c)
+    for (int e = threadIdx.x; e < nr * o; e += blockDim.x) {
+      const int r = e / o, k = e % o;
+      const float* xr = xs + r * vp;
+      const float* tk = ts + k * vp;
+      float acc = 0.f;
+      for (int c = 0; c < v; ++c) acc = fmaf(xr[c], tk[c], acc);
+      Bvo_h[Q * ov + 1LL * (a0 + r) * o + k] += static_cast<double>(acc);
+    }
+    __syncthreads();
   }
 }
 
@@ -703,15 +707,16 @@ void launch_dress_vv(const double* Bvv, const double* Bov, const double* t1, dou
                      int o, int v, cudaStream_t s) {
   static std::once_flag once;  // the attribute is process-wide: set it once, to the largest size used
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_dress_vv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 32 * 850 * 4);
-    cudaFuncSetAttribute(k_dress_vv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 32 * 850 * 4);
+    cudaFuncSetAttribute(k_dress_vv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (16 + 16) * 851 * 4);
+    cudaFuncSetAttribute(k_dress_vv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (32 + 16) * 851 * 4);
   });
   count_launch();
+  // t1 (MAXO rows) and one chunk of 16 rows of B_vv[Q], row stride v + 1
   if (o <= 16) {
-    const size_t sm = 2 * 16 * static_cast<size_t>(v) * 4;
+    const size_t sm = (16 + 16) * static_cast<size_t>(v + 1) * 4;
     k_dress_vv<16><<<naux, 256, sm, s>>>(Bvv, Bov, t1, Bvv_h, Bvo_h, o, v);
   } else {
-    const size_t sm = 2 * 32 * static_cast<size_t>(v) * 4;
+    const size_t sm = (32 + 16) * static_cast<size_t>(v + 1) * 4;
     k_dress_vv<32><<<naux, 256, sm, s>>>(Bvv, Bov, t1, Bvv_h, Bvo_h, o, v);
   }
 }

@@ -106,6 +106,50 @@ __global__ void k_pack(View v, void* out, int Kw, int ld, long long plane) {
   }
 }
 
+// The same for K contiguous in the source (K1 = K2 = 1, sk0 = 1) with every row start 16-byte aligned
+// and an even destination offset: each lane moves two consecutive k (one 16-byte load, one 4-byte store
+// per BF16 plane), 512 columns per warp item.
+__global__ void k_pack2_bf16(View v, __nv_bfloat16* out, int Kw, int ld, long long plane) {
+  const int K = v.K0;
+  const int rows = v.R2 * v.R1 * v.R0;
+  const int lane = threadIdx.x % 32;
+  const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) / 32;
+  const long long nwarp = static_cast<long long>(gridDim.x) * blockDim.x / 32;
+  const int nchunk = (Kw + 511) / 512;
+  const long long items = static_cast<long long>(rows) * nchunk;
+  const float sc = static_cast<float>(v.scale);
+  for (long long it = warp; it < items; it += nwarp) {
+    const int r = static_cast<int>(it / nchunk), ch = static_cast<int>(it % nchunk);
+    const double* src = v.src + view_roff(v, r);
+    const long long base = static_cast<long long>(r) * ld;
+    const int kend = min(Kw, (ch + 1) * 512);
+    double2 x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = ch * 512 + 2 * (lane + 32 * t);
+      if (k + 1 < K) {
+        x[t] = *reinterpret_cast<const double2*>(src + k);
+      } else {
+        x[t].x = k < K ? src[k] : 0.0;
+        x[t].y = 0.0;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = ch * 512 + 2 * (lane + 32 * t);
+      if (k < kend) {
+        const float f0 = f64_to_f32_fields(x[t].x) * sc, f1 = f64_to_f32_fields(x[t].y) * sc;
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
+        // kend is even (Kw is a multiple of 64 or an even width), so k + 1 < kend here
+        *reinterpret_cast<__nv_bfloat162*>(out + base + k) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(out + base + k + plane) = __halves2bfloat162(l0, l1);
+      }
+    }
+  }
+}
+
 // Transposing pack for sources whose rows are contiguous (sr0 == 1) and K is strided:
 // 32 x 32 tiles through shared memory so that both the reads and the writes are coalesced.
 // Blocks walk the 32 x 32 tiles grid-stride (few, long-lived blocks); a tile wholly beyond K is
@@ -157,6 +201,14 @@ static void launch_pack(const View& v, void* out, int Kw, int ld, long long plan
       k_pack_t<true><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
     else
       k_pack_t<false><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
+  } else if (bf16 && v.K1 == 1 && v.K2 == 1 && v.sk0 == 1 && Kw % 2 == 0 && ld % 2 == 0 && plane % 2 == 0 &&
+             (reinterpret_cast<uintptr_t>(out) & 3) == 0 && (reinterpret_cast<uintptr_t>(v.src) & 15) == 0 &&
+             v.sr0 % 2 == 0 && v.sr1 % 2 == 0 && v.sr2 % 2 == 0) {
+    // K contiguous, every row start 16-byte aligned (even strides from an aligned base), destination
+    // pairs 4-byte aligned
+    const long long items = static_cast<long long>(rows) * ((Kw + 511) / 512);
+    const int blocks = static_cast<int>(std::min<long long>((items + 7) / 8, 152LL * 32));
+    k_pack2_bf16<<<std::max(blocks, 1), 256, 0, s>>>(v, static_cast<__nv_bfloat16*>(out), Kw, ld, plane);
   } else {
     const long long items = static_cast<long long>(rows) * ((Kw + 255) / 256);
     const int blocks = static_cast<int>(std::min<long long>((items + 7) / 8, 152LL * 32));

@@ -166,7 +166,9 @@ def test_half_lithium_small_gap_with_triples(lnocc):
     assert (fr.nocc, fr.nvir, fr.naux, fr.seed) == (ref["nocc"], ref["nvir"], ref["naux"], ref["seed"])
     assert abs(float(fr.eps[16] - fr.eps[15]) - ref["gap"]) < 1e-15
     assert_parity(gpu_solve(lnocc, fr, 0, max_iter=300), ref, 2e-9)
-    assert_parity(gpu_solve(lnocc, fr, 1, max_iter=300, n_refine=60), ref, MIXED_TOL)
+    # refinement restarts DIIS from the best mixed amplitudes: allow as many FP64 iterations as the
+    # FP64 path needs from the MP2 guess (53 here)
+    assert_parity(gpu_solve(lnocc, fr, 1, max_iter=400, n_refine=150), ref, MIXED_TOL)
     eps, B = torch.tensor(fr.eps, device="cuda"), torch.tensor(fr.B, device="cuda")
     f = lnocc.lnocc_build_ints(16, 120, 480, eps, B, lnocc.default_opts(precision=1, max_iter=300))
     try:
