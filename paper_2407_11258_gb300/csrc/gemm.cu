@@ -154,7 +154,7 @@ __global__ void k_pack2_bf16(View v, __nv_bfloat16* out, int Kw, int ld, long lo
 // 32 x 32 tiles through shared memory so that both the reads and the writes are coalesced.
 // Blocks walk the 32 x 32 tiles grid-stride (few, long-lived blocks); a tile wholly beyond K is
 // written as zeros without reading.
-template <bool BF16>
+template <bool BF16, bool PAIRS>
 __global__ void k_pack_t(View v, void* out, int Kw, int ld, long long plane) {
   __shared__ double tile[32][33];
   const int K = v.K2 * v.K1 * v.K0;
@@ -174,10 +174,31 @@ __global__ void k_pack_t(View v, void* out, int Kw, int ld, long long plane) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) tile[ty + 8 * q][tx] = x[q];
       __syncthreads();
+      if constexpr (PAIRS) {
+        // BF16 with even widths and offsets: each thread writes two k of one row per plane (4 bytes)
+        const float sc = static_cast<float>(v.scale);
+        __nv_bfloat16* o16 = static_cast<__nv_bfloat16*>(out);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = rb + ty + 8 * q, k = kb + tx;
-        if (r < rows && k < Kw) put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ty + 8 * q], v.scale);
+        for (int q = 0; q < 2; ++q) {
+          const int p = threadIdx.x + 256 * q, rl = p / 16, kl = 2 * (p % 16);
+          const int r = rb + rl, k = kb + kl;
+          if (r < rows && k < Kw) {
+            const float f0 = f64_to_f32_fields(tile[kl][rl]) * sc, f1 = f64_to_f32_fields(tile[kl + 1][rl]) * sc;
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
+            const long long idx = static_cast<long long>(r) * ld + k;
+            *reinterpret_cast<__nv_bfloat162*>(o16 + idx) = __halves2bfloat162(h0, h1);
+            *reinterpret_cast<__nv_bfloat162*>(o16 + idx + plane) = __halves2bfloat162(l0, l1);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = rb + ty + 8 * q, k = kb + tx;
+          if (r < rows && k < Kw)
+            put<BF16>(out, static_cast<long long>(r) * ld + k, plane, tile[tx][ty + 8 * q], v.scale);
+        }
       }
       __syncthreads();
     } else {
@@ -197,10 +218,14 @@ static void launch_pack(const View& v, void* out, int Kw, int ld, long long plan
   if (transpose) {
     const long long tiles = static_cast<long long>((rows + 31) / 32) * ((Kw + 31) / 32);
     const int grid = static_cast<int>(std::min<long long>(tiles, 152LL * 8));
-    if (bf16)
-      k_pack_t<true><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
+    const bool pairs = bf16 && Kw % 2 == 0 && ld % 2 == 0 && plane % 2 == 0 &&
+                       (reinterpret_cast<uintptr_t>(out) & 3) == 0;
+    if (pairs)
+      k_pack_t<true, true><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
+    else if (bf16)
+      k_pack_t<true, false><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
     else
-      k_pack_t<false><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
+      k_pack_t<false, false><<<grid, 256, 0, s>>>(v, out, Kw, ld, plane);
   } else if (bf16 && v.K1 == 1 && v.K2 == 1 && v.sk0 == 1 && Kw % 2 == 0 && ld % 2 == 0 && plane % 2 == 0 &&
              (reinterpret_cast<uintptr_t>(out) & 3) == 0 && (reinterpret_cast<uintptr_t>(v.src) & 15) == 0 &&
              v.sr0 % 2 == 0 && v.sr1 % 2 == 0 && v.sr2 % 2 == 0) {
