@@ -131,3 +131,26 @@ def test_triples_large_nocc_and_many_los(lnocc, prec, tol, nlo):
     assert abs(etf - ofr.project(Et, fr.U_frag)) <= tol, etf - ofr.project(Et, fr.U_frag)
     assert abs(ec - ofr.project(Ec, fr.U_frag)) <= tol
     assert abs(em - ofr.project(Em, fr.U_frag)) <= tol
+
+
+@pytest.mark.parametrize("shape", [(16, 30, 120), (32, 12, 48)])
+def test_triples_lo_counts_on_the_specialised_kernels(lnocc, shape):
+    """The mixed (T) energy kernels are compiled per LO count (0, 1, 2, 4, 8; U zero-padded) and, at
+    nocc 16, per nocc; nocc 32 runs the w-only kernel. One solve, then lnocc_triples with no LOs and with
+    1, 3, 4, 6 and 8 columns of the LO matrix, each against the oracle's (T) pair matrix projected
+    with the same columns; the grouped contraction launches run at both sizes."""
+    o, v, q = shape
+    fr = synth.make_fragment(o, v, q, 5300 + o, decay=20.0, frag=tuple(range(8)))
+    r, Ec, Em, Et = _oracle_pairs(fr)
+    f = _build(lnocc, fr, 1)
+    try:
+        lnocc.lnocc_ccsd(f)
+        et0, etf0 = lnocc.lnocc_triples(f, None)
+        assert abs(et0 - np.trace(Et)) <= MIXED_TOL and etf0 == 0.0
+        for nlo in (1, 3, 4, 6, 8):
+            Un = np.ascontiguousarray(fr.U_frag[:, :nlo])
+            et, etf = lnocc.lnocc_triples(f, torch.tensor(Un, device="cuda"))
+            assert abs(et - et0) < 1e-12  # the canonical sum does not depend on the LOs
+            assert abs(etf - ofr.project(Et, Un)) <= MIXED_TOL, (nlo, etf - ofr.project(Et, Un))
+    finally:
+        f.free()
