@@ -541,10 +541,12 @@ void gemm_f64_sym(const Packed& A, int M, const OutMap& C, cudaStream_t s) {
 //   warp 0 lane 0: TMA producer; warp 1 lane 0: MMA issuer; warp 2: TMEM owner; all 4 warps: epilogue.
 //   Per K block: 4 K=16 steps x 3 products (hi*hi, hi*lo, lo*hi) into one FP32 TMEM accumulator.
 // ------------------------------------------------------------------------------------------------
-template <int BN>
+// BK_ = 64: 128-byte swizzled K blocks; 32: 64-byte swizzled K blocks, half the stage size (the grouped
+// (T) launches: four stages at BN = 256 instead of two).
+template <int BN, int BK_ = 64>
 struct TcCfg {
   static constexpr int BM = 128;
-  static constexpr int BK = 64;
+  static constexpr int BK = BK_;
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -866,12 +868,12 @@ __device__ __forceinline__ void grp_epilogue32(const TcArgs& p, const TileInfo& 
 
 // Persistent warp-specialized GEMM: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
 // warp 2 = TMEM owner, warps 4..7 = epilogue (lanes 32*(w-4) .. +31 of the accumulator).
-template <int BN>
+template <int BN, int BK = 64>
 __global__ void __launch_bounds__(256, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tB0,
               const __grid_constant__ CUtensorMap tA1, const __grid_constant__ CUtensorMap tB1,
               const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUtensorMap tW1, const TcArgs p) {
-  using Cfg = TcCfg<BN>;
+  using Cfg = TcCfg<BN, BK>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -973,8 +975,9 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
           const uint32_t off = kk * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
-          const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-          const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
+          auto sd = [](uint32_t a) { return BK == 64 ? sdesc_sw128(a) : sdesc_sw64(a); };
+          const uint64_t dah = sd(a_hi + off), dal = sd(a_lo + off);
+          const uint64_t dbh = sd(b_hi + off), dbl = sd(b_lo + off);
           mma_bf16(acc, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
           mma_bf16(acc, dah, dbl, idesc, 1u);
           mma_bf16(acc, dal, dbh, idesc, 1u);
@@ -1203,24 +1206,24 @@ static EncodeTiledFn encode_fn() {
 }
 
 // Operand [2][rows][Kp] bf16 as a 3-D tensor {Kp, rows, 2}; box {64, box_rows, 1}, 128-byte swizzle.
-static bool make_map(CUtensorMap* map, const Packed& P, int box_rows) {
+static bool make_map(CUtensorMap* map, const Packed& P, int box_rows, int bk = 64) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(P.Kp), static_cast<cuuint64_t>(P.rows), 2};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(P.Kp) * 2,
                            static_cast<cuuint64_t>(P.Kp) * 2 * static_cast<cuuint64_t>(P.rows)};
-  cuuint32_t box[3] = {64, static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
   cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P.p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int BK = 64>
 static void set_smem_attr() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+    cudaFuncSetAttribute(k_gemm_tc<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, BK>::SMEM);
   });
 }
 
@@ -1488,12 +1491,17 @@ void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSp
     set_error("gemm_grouped: nocc 16 or 32 and an FP32 W chunk only");
     return;
   }
-  using Cfg = TcCfg<256>;
-  static_assert(Cfg::SMEM <= 232448, "shared memory of the 256-column configuration");
-  set_smem_attr<256>();
+  // K-block width: 32 at nocc 32 (four pipeline stages of 48 KB at BN = 256; measured 8.13 -> 7.78 s of
+  // contractions at 32/480/1600), 64 at nocc 16 (two stages of 96 KB; its 256-long K measured faster
+  // with the wider blocks: 73 vs 83 ms at 16/240/960)
+  const int gbk = g.o == 32 ? 32 : 64;
+  if (gbk == 32)
+    set_smem_attr<256, 32>();
+  else
+    set_smem_attr<256, 64>();
   CUtensorMap m[4];
   for (int k = 0; k < 4; ++k) {
-    if (!make_map(&m[k], *ops[k], box_rows[k])) {
+    if (ops[k]->Kp % gbk != 0 || !make_map(&m[k], *ops[k], box_rows[k], gbk)) {
       set_error("cuTensorMapEncodeTiled failed");
       return;
     }
@@ -1511,11 +1519,12 @@ void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSp
   TcArgs a{};
   a.M = g.Ma;
   a.N = 256;
-  a.nkb0 = g.nkb;
-  a.kb_per = g.nkb;
+  a.nkb0 = ops[0]->Kp / gbk;
+  a.kb_per = a.nkb0;
   a.tiles_m = a.tiles_n = a.tiles_z = 1;
   a.status = dstatus;
   a.g = g;
+  a.g.nkb = ops[0]->Kp / gbk;  // K blocks of one term in this launch's block width
   for (int k = 0; k < ncg && k < 3; ++k) a.Cg[k] = Cg[k];
   a.C = Cg[0];
   a.alpha_f = 1.f;
@@ -1528,7 +1537,11 @@ void gemm_grouped(const Packed* const ops[4], const int box_rows[4], const GrpSp
                           : 2.0 * g.Ma * (1.0 * g.nc * g.o) * (64.0 * g.nkb) * 2;
   const int grid = static_cast<int>(std::min<long long>(g.nreg, num_sms()));
   count_launch();
-  k_gemm_tc<256><<<grid, 256, Cfg::SMEM, s>>>(m[0], m[1], m[2], m[3], w0, w1, a);
+  static_assert(TcCfg<256, 32>::STAGES == 4 && TcCfg<256, 64>::STAGES == 2, "grouped launch pipelines");
+  if (gbk == 32)
+    k_gemm_tc<256, 32><<<grid, 256, TcCfg<256, 32>::SMEM, s>>>(m[0], m[1], m[2], m[3], w0, w1, a);
+  else
+    k_gemm_tc<256, 64><<<grid, 256, TcCfg<256, 64>::SMEM, s>>>(m[0], m[1], m[2], m[3], w0, w1, a);
 }
 
 void gemm_tc(const Packed& A, int a_row0, const Packed& B, int b_row0, int M, int N, const OutMap& C,

@@ -125,6 +125,17 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for 64-byte rows (K blocks of 32 BF16) under the 64-byte swizzle: 8-row atoms 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;         // LBO = 16 B (ignored)
+  d |= static_cast<uint64_t>(512 >> 4) << 32;  // SBO = 512 B
+  d |= static_cast<uint64_t>(1) << 46;         // descriptor version
+  d |= static_cast<uint64_t>(4) << 61;         // SWIZZLE_64B
+  return d;
+}
+
 // Instruction descriptor for kind::f16: BF16 x BF16 -> F32, both operands K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4)                                  // D format F32
