@@ -876,6 +876,8 @@ int Frag::solve(int guess, const double* t1_in, const double* t2_in) {
       set_error(("CCSD (mixed) stopped at its noise floor with an energy spread of " + std::to_string(floor_spread) +
                  " Eh over its last iterations, above 1e-7 Eh: set opts.n_refine for FP64-residual refinement")
                     .c_str());
+    else if (n_refined > 0 && n_iter < opts.max_iter)
+      set_error("CCSD FP64 refinement did not converge within opts.n_refine iterations");
     else
       set_error("CCSD did not converge within max_iter");
     return LNOCC_ENOCONV;
