@@ -59,16 +59,16 @@ extern "C" {
  * nocc = 16 or 32 (128 rows hold whole a values; the (y, z) plane is one or four 256-column
  * accumulator tiles); AUTO takes it there and PER_TERM elsewhere, and GROUPED falls back to PER_TERM
  * for other nocc. */
+#define LNOCC_TK_AUTO 0
+#define LNOCC_TK_PER_TERM 1
+#define LNOCC_TK_GROUPED 2
+
 /* Device memory of a handle (and of its lnocc_triples temporaries). CACHED: stream-ordered allocations
  * from one library-wide pool per device that keeps freed memory for later handles (no cudaMalloc /
  * cudaFree, and no device synchronisation, once the pool holds enough; lnocc_trim_pool returns the
  * unused part to the device). DIRECT: cudaMalloc / cudaFree per buffer. */
 #define LNOCC_MEM_CACHED 0
 #define LNOCC_MEM_DIRECT 1
-
-#define LNOCC_TK_AUTO 0
-#define LNOCC_TK_PER_TERM 1
-#define LNOCC_TK_GROUPED 2
 
 #define LNOCC_FAULT_NAN_INPUT 1 /* fault injection (host side): poison one element of the B copy */
 #define LNOCC_FAULT_ZERO_DIIS 2 /* fault injection: run without DIIS extrapolation */
@@ -95,7 +95,7 @@ typedef struct lnocc_opts {
                            workspace size that lnocc_workspace_bytes reports */
   int triples_kernel;   /* (T) contraction launches on the mixed path: LNOCC_TK_AUTO (0, the default),
                            LNOCC_TK_PER_TERM or LNOCC_TK_GROUPED (same W, same energy) */
-  int memory;           /* LNOCC_MEM_CACHED (0, the default) or LNOCC_MEM_DIRECT, see below */
+  int memory;           /* LNOCC_MEM_CACHED (0, the default) or LNOCC_MEM_DIRECT (see their definitions) */
   int reserved[2];
 } lnocc_opts;
 
