@@ -178,7 +178,9 @@ int lnocc_fragment_energy(lnocc_frag* f, int nlo, const double* U_frag, double* 
  *   e_t_frag (host)         : sum_alpha sum_ii' U_i,alpha E_ii',(T) U_i',alpha (may be NULL).
  * FP64 precision: FP64 contractions and energy arithmetic. Mixed precision: the W contractions as
  * BF16x3/FP32 on tensor cores; the denominators' terms formed in FP64, the scaled w and v, their
- * products and the i-sums in FP32, every block sum and the total in FP64.
+ * products and the i-sums in FP32; a block's partials summed in compensated FP32 (the rounding error
+ * of every addition carried alongside, both converted to FP64 once per block) by the staged kernels,
+ * in FP64 by the generic one; the sums over blocks and the total in FP64.
  * Any nocc and any number of LOs (up to 8 LOs and while a block of the (T) energy fits shared memory the
  * staged energy kernels run; otherwise a generic kernel that stages nothing).
  * Temporaries (the packed (T) operands, a W chunk of at most opts.triples_chunk_mb or one b-slab, the

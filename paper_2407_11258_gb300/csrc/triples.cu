@@ -40,6 +40,55 @@ namespace {
 // Position permutations of three slots, listed as (p1, p2, p3) in 0-based slots.
 __constant__ int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
+// Compensated FP32 summation for the FP32 block-energy kernels: a running sum s and the sum c of the
+// rounding errors of its additions, each error obtained exactly by Knuth's TwoSum (TAOCP vol. 2,
+// 4.2.2), cascaded as in the Sum2 algorithm of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 1955
+// (2005)). s + c is as accurate as a sum formed in twice the FP32 precision (error about
+// u|S| + (n u)^2 sum|x_i|, u = 2^-24), which keeps the block partials as accurate as the FP64 sums
+// they replace without FP64-pipe work (the part's FP64 rate is a small fraction of its FP32 rate).
+// The _rn intrinsics keep the compiler from fusing or reordering the error terms.
+struct CSum {
+  float s, c;
+};
+__device__ __forceinline__ void csum_add(CSum& a, float x) {
+  const float t = __fadd_rn(a.s, x);
+  const float bp = __fsub_rn(t, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  a.s = t;
+  a.c = __fadd_rn(a.c, err);
+}
+__device__ __forceinline__ void csum_merge(CSum& a, const CSum& b) {
+  csum_add(a, b.s);
+  a.c = __fadd_rn(a.c, b.c);
+}
+// Block result {canonical, projected} of two compensated sums: warp trees, then warp 0 over the warps'
+// sums, in a fixed order; thread 0 writes -(s + c) / 3 in FP64 (the 1/3 of the six orderings).
+__device__ __forceinline__ void csum_block_out(CSum e0, CSum e1, double* out, long long blk_id) {
+  __shared__ float4 sh[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    CSum o0, o1;
+    o0.s = __shfl_xor_sync(0xffffffffu, e0.s, off);
+    o0.c = __shfl_xor_sync(0xffffffffu, e0.c, off);
+    o1.s = __shfl_xor_sync(0xffffffffu, e1.s, off);
+    o1.c = __shfl_xor_sync(0xffffffffu, e1.c, off);
+    csum_merge(e0, o0);
+    csum_merge(e1, o1);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) sh[w] = make_float4(e0.s, e0.c, e1.s, e1.c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CSum a0{0.f, 0.f}, a1{0.f, 0.f};
+    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
+      const float4 t = sh[q];
+      csum_merge(a0, CSum{t.x, t.y});
+      csum_merge(a1, CSum{t.z, t.w});
+    }
+    out[2 * blk_id] = -(static_cast<double>(a0.s) + static_cast<double>(a0.c)) / 3.0;
+    out[2 * blk_id + 1] = -(static_cast<double>(a1.s) + static_cast<double>(a1.c)) / 3.0;
+  }
+}
+
 // Block energy, generic form: one CTA per (pair, a) with a <= b; threads over (j, k). Any nocc and any
 // number of LOs: the projected i-sums are kept for up to kLoChunk LOs at a time, and for more LOs the
 // i loop is repeated per chunk (the canonical part is accumulated in the first pass only). W is FP64
@@ -323,9 +372,10 @@ __global__ void k_t_energy_staged(const TW* __restrict__ W, long long slot_strid
   }
 }
 
-// Block energy of the mixed path with w and v both staged (FP32 W): the same quantities, orderings and
-// summation order as k_t_energy_staged with Real = float and both w and v staged (the form it replaced
-// on this path), with the data movement reworked:
+// Block energy of the mixed path with w and v both staged (FP32 W): the same quantities and orderings
+// as k_t_energy_staged with Real = float and both w and v staged (the form it replaced on this path),
+// with the data movement reworked and the partials across (j, k) summed in compensated FP32 (CSum)
+// instead of FP64:
 //  * the staging pass issues eight independent W loads per thread before it uses any of them;
 //  * w and v of one (y0, y1, y2) sit side by side, so a placement is one 8-byte shared-memory load;
 //  * the projected i-sums of z and y for one LO form a pair updated by one packed FP32 FMA, with
@@ -357,7 +407,6 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
   // U pairs (U[i][al], U[i][al]), 16-byte aligned for 128-bit loads
   const int uoff = (2 * blk + 3 * o2p + 4 * o + 3) & ~3;
   float* U2 = reinterpret_cast<float*>(smraw) + uoff;
-  const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
   // (pa|qb) etc. from the FP32 copy ovT[x][y][p][q] = (px|qy): o^2 consecutive floats per slice
   const float* oab = ovT + (1LL * a * v + b) * o2;
   const float* oac = ovT + (1LL * a * v + c) * o2;
@@ -369,6 +418,7 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
     Sbc[p * P1 + q] = obc[idx];
   }
   for (int y = threadIdx.x; y < o; y += blockDim.x) {
+    const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;  // FP64 in these o threads only
     ta[y] = static_cast<float>(t1[y * v + a]);
     tb[y] = static_cast<float>(t1[y * v + b]);
     tc[y] = static_cast<float>(t1[y * v + c]);
@@ -425,7 +475,8 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
     act[pi] = !dup;
   }
   constexpr int NL = NLO > 0 ? NLO : 1;
-  double r_can = 0, r_frag = 0;  // FP32 sums run over one (j, k) only; partials across (j, k) in FP64
+  // FP32 sums run over one (j, k) only; partials across (j, k) in compensated FP32 (CSum)
+  CSum r_can{0.f, 0.f}, r_frag{0.f, 0.f};
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
     int off[6], si[6];
@@ -483,13 +534,13 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
           }
         }
       }
-      r_can += static_cast<double>(acc);
+      csum_add(r_can, acc);
       float f = 0.f;
 #pragma unroll
       for (int h = 0; h < 3; ++h)
 #pragma unroll
         for (int al = 0; al < NLO; ++al) f += zp[h][al].x * zp[h][al].y;
-      r_frag += static_cast<double>(f);
+      csum_add(r_frag, f);
       continue;
     }
     float2 zy[6][NL];  // (sum_i U z, sum_i U y) per ordering and LO
@@ -530,35 +581,15 @@ __global__ void __launch_bounds__(256, NLO <= 2 ? 4 : 2)
         for (int al = 0; al < NLO; ++al) zy[pi][al] = __ffma2_rn(u2[al], zyv, zy[pi][al]);
       }
     }
-    r_can += static_cast<double>(acc);
+    csum_add(r_can, acc);
     float f = 0.f;
 #pragma unroll
     for (int pi = 0; pi < 6; ++pi)
 #pragma unroll
       for (int al = 0; al < NLO; ++al) f += zy[pi][al].x * zy[pi][al].y;
-    r_frag += static_cast<double>(f);
+    csum_add(r_frag, f);
   }
-  double e_can = r_can, e_frag = r_frag;
-  __shared__ double sh[2][32];
-  for (int off = 16; off > 0; off >>= 1) {
-    e_can += __shfl_xor_sync(0xffffffffu, e_can, off);
-    e_frag += __shfl_xor_sync(0xffffffffu, e_frag, off);
-  }
-  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  if (l == 0) {
-    sh[0][w] = e_can;
-    sh[1][w] = e_frag;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
-      s0 += sh[0][q];
-      s1 += sh[1][q];
-    }
-    out[2 * blk_id] = -s0 / 3.0;
-    out[2 * blk_id + 1] = -s1 / 3.0;
-  }
+  csum_block_out(r_can, r_frag, out, blk_id);
 }
 
 // Block energy of the mixed path when only w fits in shared memory (nocc 29..35 at 200 KB): w = W s is
@@ -591,7 +622,6 @@ __global__ void __launch_bounds__(NLO <= 2 ? 512 : 256, 1)
   float* dm = tc + o;
   const int uoff = (blk + 3 * o2p + 4 * o + 3) & ~3;
   float* U2 = sw + uoff;  // (U[i][al], U[i][al]) pairs
-  const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;
   const float* oab = ovT + (1LL * a * v + b) * o2;
   const float* oac = ovT + (1LL * a * v + c) * o2;
   const float* obc = ovT + (1LL * b * v + c) * o2;
@@ -602,6 +632,7 @@ __global__ void __launch_bounds__(NLO <= 2 ? 512 : 256, 1)
     Sbc[p * P1 + q] = obc[idx];
   }
   for (int y = threadIdx.x; y < o; y += blockDim.x) {
+    const double ex3 = (eps[o + a] + eps[o + b] + eps[o + c]) / 3.0;  // FP64 in these o threads only
     ta[y] = static_cast<float>(t1[y * v + a]);
     tb[y] = static_cast<float>(t1[y * v + b]);
     tc[y] = static_cast<float>(t1[y * v + c]);
@@ -648,7 +679,8 @@ __global__ void __launch_bounds__(NLO <= 2 ? 512 : 256, 1)
     act[pi] = !dup;
   }
   constexpr int NL = NLO > 0 ? NLO : 1;
-  double r_can = 0, r_frag = 0;  // FP32 sums over one (j, k); partials across (j, k) in FP64
+  // FP32 sums over one (j, k); partials across (j, k) in compensated FP32 (CSum)
+  CSum r_can{0.f, 0.f}, r_frag{0.f, 0.f};
   for (int jk = threadIdx.x; jk < o2; jk += blockDim.x) {
     const int j = jk / o, k = jk % o;
     int off[6], si[6];
@@ -733,35 +765,15 @@ __global__ void __launch_bounds__(NLO <= 2 ? 512 : 256, 1)
         }
       }
     }
-    r_can += static_cast<double>(acc);
+    csum_add(r_can, acc);
     float f = 0.f;
 #pragma unroll
     for (int pi = 0; pi < 6; ++pi)
 #pragma unroll
       for (int al = 0; al < NLO; ++al) f += zy[pi][al].x * zy[pi][al].y;
-    r_frag += static_cast<double>(f);
+    csum_add(r_frag, f);
   }
-  double e_can = r_can, e_frag = r_frag;
-  __shared__ double sh[2][32];
-  for (int offs = 16; offs > 0; offs >>= 1) {
-    e_can += __shfl_xor_sync(0xffffffffu, e_can, offs);
-    e_frag += __shfl_xor_sync(0xffffffffu, e_frag, offs);
-  }
-  const int wi = threadIdx.x / 32, l = threadIdx.x % 32;
-  if (l == 0) {
-    sh[0][wi] = e_can;
-    sh[1][wi] = e_frag;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int q = 0; q < static_cast<int>(blockDim.x / 32); ++q) {
-      s0 += sh[0][q];
-      s1 += sh[1][q];
-    }
-    out[2 * blk_id] = -s0 / 3.0;
-    out[2 * blk_id + 1] = -s1 / 3.0;
-  }
+  csum_block_out(r_can, r_frag, out, blk_id);
 }
 
 // Per-c tables of the batched (T) terms, one entry per (b, c >= b) in b-major order (the order of the
