@@ -174,3 +174,36 @@ def test_binding_rejects_mis_sized_arrays_before_the_call(lib):
         m.set_norm(np.zeros(16))
     with pytest.raises(ValueError, match="dt"):
         m.train_step(torch.zeros(4, lnocc.NFEAT, dtype=torch.float32), torch.zeros(3, dtype=torch.float32), 1e-3)
+
+
+def test_workspace_queries_need_no_gpu(lib):
+    """lnocc_workspace_bytes / lnocc_mp2_workspace_bytes are host arithmetic: bad arguments give
+    EINVAL, the (T) scratch grows with the W-chunk bound until the chunk holds the largest b-slab
+    ((b + 1)(v - b) nocc^3 elements) and stays constant beyond it, FP32 W needs less than FP64 W, and
+    it always holds at least one chunk of W for the largest slab's single c (v nocc^3 elements)."""
+    with pytest.raises(lnocc.LnoccError):
+        lnocc.lnocc_workspace_bytes(0, 24, 96)
+    with pytest.raises(lnocc.LnoccError):
+        lnocc.lnocc_workspace_bytes(4, 24, 96, lnocc.default_opts(precision=5))
+    with pytest.raises(lnocc.LnoccError):
+        lnocc.lnocc_workspace_bytes(4, 24, 96, lnocc.default_opts(triples_chunk_mb=-1))
+    with pytest.raises(lnocc.LnoccError):
+        lnocc.lnocc_mp2_workspace_bytes(2, 4, 24, 96)
+    b = ctypes.c_longlong(0)
+    assert lib.lnocc_workspace_bytes(4, 24, 96, None, None) == lnocc.LNOCC_EINVAL
+    assert lib.lnocc_workspace_bytes(4, 24, 96, None, ctypes.byref(b)) == lnocc.LNOCC_OK and b.value > 0
+    o, v, q = 8, 60, 240
+    max_slab = max((bb + 1) * (v - bb) for bb in range(v)) * o ** 3
+    for prec, esz in ((lnocc.LNOCC_PREC_FP64, 8), (lnocc.LNOCC_PREC_MIXED, 4)):
+        sizes = [lnocc.lnocc_workspace_bytes(o, v, q, lnocc.default_opts(precision=prec, triples_chunk_mb=mb))
+                 for mb in (1, 2, 4, 8, 768, 4096)]
+        assert all(x <= y for x, y in zip(sizes, sizes[1:]))
+        assert sizes[0] >= v * o ** 3 * esz
+        assert sizes[-1] == sizes[-2]  # 768 MB already holds the largest slab
+        assert sizes[-1] - sizes[0] <= max_slab * esz
+    assert (lnocc.lnocc_workspace_bytes(o, v, q, lnocc.default_opts(precision=lnocc.LNOCC_PREC_MIXED))
+            < lnocc.lnocc_workspace_bytes(o, v, q, lnocc.default_opts(precision=lnocc.LNOCC_PREC_FP64)))
+    for prec in (lnocc.LNOCC_PREC_FP64, lnocc.LNOCC_PREC_MIXED):
+        small, large = (lnocc.lnocc_mp2_workspace_bytes(prec, 4, 24, 96),
+                        lnocc.lnocc_mp2_workspace_bytes(prec, 16, 240, 960))
+        assert 0 < small < large
